@@ -1,0 +1,329 @@
+"""Benchmark of the fused metric-evolution chain on GB300 (one JSON line on stdout).
+
+A step is one pass of the fused forward chain (inverse metric -> Christoffel symbols -> covariant
+derivative of the shift -> d_t g_ij) over one grid of N = 2^24 (256^3) points with the seeded random
+grid recipe, all 43 inputs and 39 outputs resident in HBM.  The metric is grid points per second;
+achieved HBM GB/s counts the paper's effective bandwidth, 8 bytes x (43 + 39) components x N per pass
+(Eq. 22).  Inputs plus outputs (11 GB) exceed the 129 MB L2, so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--variant f64|f64_ff|f32]
+
+Under torchrun every rank runs its own grid (the points are independent; no collective on the data
+path): weak scaling, value = all ranks' points / max over ranks of the timed region.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "grid points/s and HBM GB/s, fused Christoffel+dt g_ij, fwd and fwd+adjoint"
+UNIT = "grid points/s"
+N_FULL = 1 << 24
+BYTES_PER_POINT = {"f64": 656, "f64_ff": 656, "f32": 328}
+KERNEL_NAME = {"f64": "dtg_fwd_f64_kernel", "f64_ff": "dtg_fwd_ff_kernel", "f32": "dtg_fwd_f32_kernel"}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--variant", default=os.environ.get("TL_BENCH_VARIANT", "f64"), choices=["f64", "f64_ff", "f32"])
+    ap.add_argument("--n", type=int, default=N_FULL)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the secondary variant measurements")
+    return ap.parse_args()
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def src_digest():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1804_10120_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(name.encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_per_launch(kernel, n):
+    """DRAM bytes per launch from the committed ncu summary, scaled to n points; None when the kernel
+    sources changed since the capture (or none exists)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        e = d[kernel]
+        if e.get("src_digest") != src_digest():
+            return None
+        return float(e["dram_bytes"]) * n / float(e["n"])
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples during the timed region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.out, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.out.close()
+
+    def summary(self):
+        if self.proc is None or not self.path:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 7:
+                    try:
+                        rows.append((float(parts[0]), float(parts[1]), parts[3:7]))
+                    except ValueError:
+                        pass
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i in range(4) if r[i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_threads():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def time_oracle(x_host, budget_s=10.0, max_s=30.0):
+    """The oracle as it stands, on all host cores, over the first points of the workload grid, repeated
+    until ~budget_s of CPU work.  Returns (points/s, threads, sample description)."""
+    import numpy as np
+    import oracle
+    threads = cpu_threads()
+    n = x_host.shape[1]
+    out = np.empty((39, n), dtype=np.float64)
+    reps, points = 0, 0
+    t0 = time.perf_counter()
+    while True:
+        oracle.forward_threaded(x_host, out, threads)
+        reps += 1
+        points += n
+        el = time.perf_counter() - t0
+        if el >= budget_s or el + el / reps > max_s:
+            break
+    return points / el, threads, "%d pass(es) of the oracle over %d points of the workload grid, %.1f s" % (reps, n, el)
+
+
+def reference_arm(args):
+    """The oracle (plain CPU loop nest) as the reference implementation, on this host's cores."""
+    import numpy as np
+    import gridgen
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    n_sample = min(args.n, 1 << 22)
+    x = gridgen.random_grid(n_sample, 1)
+    import oracle
+    threads = cpu_threads()
+    out = np.empty((39, n_sample), dtype=np.float64)
+    for _ in range(max(1, min(args.warmup, 1))):
+        oracle.forward_threaded(x, out, threads)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.forward_threaded(x, out, threads)
+        times.append(time.perf_counter() - t0)
+    t = sum(times)
+    value = n_sample * args.steps / t
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded random grid)",
+        "config": {"workload": "fused forward, single grid N=2^24 (256^3) FP64 SoA, seed 1; each reference step "
+                               "runs the CPU oracle on the first %d points" % n_sample,
+                   "global_batch": n_sample, "parallelism": "host threads"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": "%d points per step (first points of the N=2^24 seed-1 grid)" % n_sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    import gridgen
+    import paper_1804_10120_gb300 as tl
+    from paper_1804_10120_gb300 import build as tlbuild
+
+    world, rank, local = dist_setup()
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    tlbuild.build()
+    tl.lib()
+
+    n = args.n
+    variant = args.variant
+    td = torch.float32 if variant == "f32" else torch.float64
+    esz = 4 if variant == "f32" else 8
+    x_host = gridgen.random_grid(n, 1 + 1000 * rank)
+    x_pinned = torch.from_numpy(x_host).to(td).pin_memory()
+    x = x_pinned.to(dev)
+    y = torch.empty((39, n), dtype=td, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        tl.tl_dtg_forward(x, y, dtype=variant, stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    with ClockSampler(dev.index) as clk:
+        ev[0].record(stream)
+        for i in range(args.steps):
+            step()
+            ev[i + 1].record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    per = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
+    total_ms = ev[0].elapsed_time(ev[-1])
+    t_max = total_ms
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = world * n * args.steps / (t_max * 1e-3)
+    avg_launch_s = statistics.mean(per) * 1e-3
+    hbm, peak_kind = peaks()
+    bpp = BYTES_PER_POINT[variant]
+    achieved = bpp * n / avg_launch_s / 1e9
+    traffic = traffic_per_launch(KERNEL_NAME[variant], n)
+
+    # end to end through the host-buffer C entry point: H2D of the inputs and D2H of the outputs inside
+    # the timed region, page-locked host memory
+    e2e = None
+    if not args.no_e2e:
+        y_pinned = torch.empty((39, n), dtype=td).pin_memory()
+        ws = torch.empty(max(16, tl.tl_dtg_host_workspace_bytes(n, variant)), dtype=torch.uint8, device=dev)
+        e2e_steps = max(1, min(args.steps, 5))
+        tl.tl_dtg_forward_host(x_pinned, y_pinned, ws, dtype=variant, stream=stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(e2e_steps):
+            tl.tl_dtg_forward_host(x_pinned, y_pinned, ws, dtype=variant, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e_ms = e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([e_ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e_ms = float(t.item())
+        e2e = {"value": world * n * e2e_steps / (e_ms * 1e-3), "unit": UNIT,
+               "h2d_bytes_per_step": 43 * n * esz, "d2h_bytes_per_step": 39 * n * esz,
+               "steps": e2e_steps, "entry_point": "tl_dtg_forward_host"}
+        del ws, y_pinned
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        v, cores, sample = time_oracle(x_host)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"f64": "f64", "f64_ff": "f64", "f32": "f32"}[variant],
+            "data": "synthetic (seeded random grid: g = delta + 0.1 S, dg ~ U[-0.1,0.1], K, beta, dbeta ~ N(0,0.1), alpha ~ U[0.5,1.5])",
+            "config": {"workload": "fused forward chain, single grid N=2^24 (256^3), SoA, seed 1",
+                       "variant": variant, "global_batch": world * n, "points_per_gpu": n,
+                       "parallelism": "replicas (independent grids per GPU)" if world > 1 else "single GPU",
+                       "l2": "inputs+outputs %.1f GB > 129 MB L2; no flush" % (82 * n * esz / 1e9)},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "traffic": traffic, "peak_source": peak_kind,
+                         "kernel": KERNEL_NAME[variant], "bytes_per_point": bpp,
+                         "avg_launch_ms": avg_launch_s * 1e3},
+            "gpu_launches": args.steps,
+            "clocks": clk.summary(),
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

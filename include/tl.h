@@ -1,0 +1,118 @@
+/*
+ * tl.h -- C ABI of the fused metric-evolution kernels (sm_103a).
+ *
+ * At every point of an N-point grid the library evaluates, in one fused kernel, the chain of
+ * Lewis & Pfeiffer, "Automatic generation of CUDA code performing tensor manipulations using C++
+ * expression templates" (arXiv:1804.10120):
+ *   1. g^ij, the inverse of the symmetric spatial metric g_ij (Sec. 1, after Eq. 3: "the inverse");
+ *   2. the Christoffel symbols Gamma^i_jk = 1/2 g^il (d_k g_jl + d_j g_lk - d_l g_jk)   (Eq. 3);
+ *   3. the covariant derivative of the shift nabla_j beta_i = d_j beta_i - Gamma^k_ij beta_k
+ *      (footnote to Listing 1);
+ *   4. d_t g_ij = -2 alpha K_ij + nabla_i beta_j + nabla_j beta_i   (Eq. 2);
+ * its adjoint (reverse-mode derivative; the paper has none), and a batched form that runs many
+ * multi-domain subgrids (Sec. 1: "for multi-domain methods, on multiple spatial grids") in one launch.
+ *
+ * Data layout.  Structure of arrays: every tensor component is its own array of n elements (the
+ * paper's Tensor<DataMesh>, Sec. 2), and a symmetric index pair is stored once (Sec. 2, lookup table).
+ * Packed symmetric order p(i,j), i<=j:  (0,0)=0 (0,1)=1 (0,2)=2 (1,1)=3 (1,2)=4 (2,2)=5.
+ *   inputs   g[p] = g_ij;  dg[3p+k] = d_k g_ij (derivative index innermost, as dg(i,j)(k) in
+ *            Listing 4);  K[p] = K_ij;  alpha;  beta[i] = beta_i;  dbeta[3i+j] = d_j beta_i
+ *   outputs  ginv[p] = g^ij;  gamma[6i + p(j,k)] = Gamma^i_jk;  dbcov[3i+j] = nabla_j beta_i;
+ *            dtg[p] = d_t g_ij
+ * Every table entry is a DEVICE pointer unless the function says otherwise.  Element type: double
+ * for TL_F64 and TL_F64_FF, float for TL_F32.  Arrays need only element alignment (8 or 4 bytes).
+ *
+ * Ownership and ordering.  The caller owns every array.  tl_dtg_forward / tl_dtg_backward /
+ * tl_dtg_batched allocate nothing, never synchronise, and only enqueue work on `stream` (NULL = the
+ * legacy default stream); their results are ready when that stream reaches the enqueued work.
+ * Outputs must not overlap inputs or each other (checked on the host: TL_ERR_INVALID_ARG).
+ *
+ * Errors.  Every function returns a status; no exception crosses the ABI.  Arguments are checked
+ * before anything is enqueued, so a non-OK status means nothing was launched.  tl_last_error() returns
+ * a thread-local message describing the last non-OK status of the calling thread.
+ */
+#ifndef TL_H
+#define TL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define TL_API __attribute__((visibility("default")))
+#else
+#define TL_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t (CUDA's runtime defines cudaStream_t as struct CUstream_st *). */
+typedef struct CUstream_st *tl_stream;
+
+typedef enum {
+    TL_OK = 0,
+    TL_ERR_INVALID_ARG = 1,    /* NULL pointer, n < 0, overlapping outputs, bad dtype or size      */
+    TL_ERR_ALIGNMENT = 2,      /* an array not aligned to its element size                         */
+    TL_ERR_UNSUPPORTED = 3,    /* no sm_103a device / combination not provided                     */
+    TL_ERR_CUDA = 4,           /* a CUDA runtime call or launch failed (message in tl_last_error) */
+    TL_ERR_TIMEOUT = 5,        /* a bounded device-side wait gave up (batched status word)         */
+    TL_ERR_PLAN_MISMATCH = 6   /* a batch plan used with another device or after destruction       */
+} tl_status;
+
+typedef enum {
+    TL_F64 = 0,      /* binary64 storage; every arithmetic operation in IEEE binary64              */
+    TL_F32 = 1,      /* binary32 storage and arithmetic; det(g) and the 3x3 inverse in binary64    */
+    TL_F64_FF = 2    /* binary64 storage; inverse, Eq. 3 bracket and Eq. 2 in binary64; the two
+                        contractions (raising Eq. 3 with g^il, and Gamma^k_ij beta_k) in float-float
+                        arithmetic (pairs of binary32, >= 46 significant bits) on the FP32 pipes   */
+} tl_dtype;
+
+/* Component pointer tables (43 inputs, 39 outputs); layout as described above. */
+typedef struct { const void *g[6], *dg[18], *K[6], *alpha, *beta[3], *dbeta[9]; } tl_dtg_in;
+typedef struct { void *ginv[6], *gamma[18], *dbcov[9], *dtg[6]; } tl_dtg_out;
+/* Upstream gradients, laid out like the outputs.  A NULL entry means that output does not enter the
+ * functional (treated as an all-zero array, and never read). */
+typedef struct { const void *ginv[6], *gamma[18], *dbcov[9], *dtg[6]; } tl_dtg_gout;
+/* Input gradients, laid out like the inputs; all 43 required. */
+typedef struct { void *g[6], *dg[18], *K[6], *alpha, *beta[3], *dbeta[9]; } tl_dtg_gin;
+
+/*
+ * Forward chain (steps 1-4 above) over n points: reads the 43 input arrays, writes the 39 output
+ * arrays.  n == 0 returns TL_OK and launches nothing.  A point whose metric is singular yields
+ * non-finite outputs (the definition divides by det g); no status reports it.
+ */
+TL_API tl_status tl_dtg_forward(const tl_dtg_in *in, const tl_dtg_out *out, int64_t n, tl_dtype dtype,
+                         tl_stream stream);
+
+/*
+ * Adjoint: with L = sum over points and outputs of gout * out, writes dL/d(input) for every stored
+ * input element into gin.  A symmetric input stored once receives the sum over both index orders.
+ * g^ij and Gamma are recomputed from the inputs, not read.  Same rules as tl_dtg_forward; gin must
+ * not overlap in or gout.
+ */
+TL_API tl_status tl_dtg_backward(const tl_dtg_in *in, const tl_dtg_gout *gout, const tl_dtg_gin *gin, int64_t n,
+                          tl_dtype dtype, tl_stream stream);
+
+/*
+ * Forward with HOST arrays (end-to-end form): copies the 43 input arrays host->device into `workspace`,
+ * runs tl_dtg_forward there and copies the 39 outputs device->host, all enqueued on `stream`, in
+ * chunks so that copies in both directions overlap the kernel.  `in` and `out` hold HOST pointers
+ * (page-locked memory gives full copy bandwidth; pageable memory works but the copies then
+ * synchronise).  `workspace` is a DEVICE buffer of at least tl_dtg_host_workspace_bytes(n, dtype)
+ * bytes owned by the caller.  Returns after enqueueing; the host outputs are valid once `stream`
+ * completes.
+ */
+TL_API size_t tl_dtg_host_workspace_bytes(int64_t n, tl_dtype dtype);
+TL_API tl_status tl_dtg_forward_host(const tl_dtg_in *in, const tl_dtg_out *out, int64_t n, tl_dtype dtype,
+                              void *workspace, size_t workspace_bytes, tl_stream stream);
+
+TL_API const char *tl_status_string(tl_status s);
+TL_API const char *tl_last_error(void);
+/* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
+TL_API int tl_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TL_H */

@@ -1,0 +1,263 @@
+"""Python binding of the tl C ABI (include/tl.h): argument marshalling only.
+
+Every step of the metric-evolution chain runs in the CUDA library ``libtl.so`` built from ``csrc/``
+for sm_103a; this module only turns torch tensors into component pointer tables and calls the C
+entry points of the same names.  There is no fallback: if the library is missing or the device is
+not an sm_103 GPU, calls raise ``TLError``.
+
+Array convention: a [43, n] tensor holds the inputs (g[6], dg[18], K[6], alpha, beta[3], dbeta[9])
+and a [39, n] tensor the outputs (ginv[6], gamma[18], dbcov[9], dtg[6]); any sequence of 43 (39)
+1-D tensors with unit stride works as well.
+"""
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+N_IN = 43
+N_OUT = 39
+TL_F64, TL_F32, TL_F64_FF = 0, 1, 2
+DTYPES = {"f64": TL_F64, "f32": TL_F32, "f64_ff": TL_F64_FF}
+STATUS = {0: "TL_OK", 1: "TL_ERR_INVALID_ARG", 2: "TL_ERR_ALIGNMENT", 3: "TL_ERR_UNSUPPORTED",
+          4: "TL_ERR_CUDA", 5: "TL_ERR_TIMEOUT", 6: "TL_ERR_PLAN_MISMATCH"}
+
+_lib = None
+_lock = threading.Lock()
+
+
+class TLError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__("%s: %s" % (STATUS.get(status, status), message))
+        self.status = status
+
+
+PtrTab43 = ctypes.c_void_p * N_IN
+PtrTab39 = ctypes.c_void_p * N_OUT
+
+
+def library_path():
+    return _build.LIB
+
+
+def lib():
+    """Load libtl.so (built in-tree by build()); raises if it is absent."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if not os.path.exists(path):
+                raise TLError(3, "libtl.so is not built (%s); call paper_1804_10120_gb300.build.build()" % path)
+            L = ctypes.CDLL(path)
+            vp, i64, i32, sz = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_size_t
+            L.tl_dtg_forward.argtypes = [vp, vp, i64, i32, vp]
+            L.tl_dtg_backward.argtypes = [vp, vp, vp, i64, i32, vp]
+            L.tl_dtg_forward_host.argtypes = [vp, vp, i64, i32, vp, sz, vp]
+            L.tl_dtg_host_workspace_bytes.argtypes = [i64, i32]
+            L.tl_dtg_host_workspace_bytes.restype = sz
+            for f in (L.tl_dtg_forward, L.tl_dtg_backward, L.tl_dtg_forward_host):
+                f.restype = i32
+            L.tl_status_string.argtypes = [i32]
+            L.tl_status_string.restype = ctypes.c_char_p
+            L.tl_last_error.argtypes = []
+            L.tl_last_error.restype = ctypes.c_char_p
+            L.tl_version.restype = i32
+            _lib = L
+    return _lib
+
+
+def _check(status):
+    if status != 0:
+        raise TLError(status, lib().tl_last_error().decode())
+
+
+def _dtype_code(dtype):
+    if isinstance(dtype, int):
+        return dtype
+    return DTYPES[dtype]
+
+
+def _torch_dtype(code):
+    import torch
+    return torch.float32 if code == TL_F32 else torch.float64
+
+
+def _rows(t, count, name, allow_none=False):
+    """Tensor [count, n] or a sequence of count 1-D tensors -> list of 1-D tensors (None kept)."""
+    if hasattr(t, "dim") and t.dim() == 2:
+        if t.shape[0] != count:
+            raise ValueError("%s must have %d rows, got %d" % (name, count, t.shape[0]))
+        return [t[s] for s in range(count)]
+    rows = list(t)
+    if len(rows) != count:
+        raise ValueError("%s must hold %d arrays, got %d" % (name, count, len(rows)))
+    if not allow_none and any(r is None for r in rows):
+        raise ValueError("%s may not contain None" % name)
+    return rows
+
+
+def _table(rows, count, n, tdtype, device_type, name):
+    tab = (ctypes.c_void_p * count)()
+    for s, r in enumerate(rows):
+        if r is None:
+            tab[s] = None
+            continue
+        if r.dim() != 1 or r.shape[0] != n or (n > 1 and r.stride(0) != 1):
+            raise ValueError("%s[%d] must be a unit-stride 1-D tensor of length %d" % (name, s, n))
+        if r.dtype != tdtype:
+            raise TypeError("%s[%d] has dtype %s, expected %s" % (name, s, r.dtype, tdtype))
+        if r.device.type != device_type:
+            raise ValueError("%s[%d] must be on %s" % (name, s, device_type))
+        tab[s] = r.data_ptr() if n > 0 else None
+    return tab
+
+
+def _stream_handle(stream, device):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream(device)
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _nonnull_empty(tab, count):
+    # n == 0: the C ABI still wants non-NULL table entries; any non-NULL value is fine as nothing is read.
+    for s in range(count):
+        if tab[s] is None:
+            tab[s] = 16
+
+
+def tl_dtg_forward(inputs, outputs=None, dtype="f64", stream=None):
+    """Forward chain on device tensors.  Returns the [39, n] outputs (allocated if not given)."""
+    import torch
+    code = _dtype_code(dtype)
+    td = _torch_dtype(code)
+    rows = _rows(inputs, N_IN, "inputs")
+    n = rows[0].shape[0]
+    dev = rows[0].device
+    if outputs is None:
+        outputs = torch.empty((N_OUT, n), dtype=td, device=dev)
+    orows = _rows(outputs, N_OUT, "outputs")
+    itab = _table(rows, N_IN, n, td, "cuda", "inputs")
+    otab = _table(orows, N_OUT, n, td, "cuda", "outputs")
+    if n == 0:
+        _nonnull_empty(itab, N_IN)
+        _nonnull_empty(otab, N_OUT)
+    with torch.cuda.device(dev):
+        _check(lib().tl_dtg_forward(ctypes.byref(itab), ctypes.byref(otab), n, code, _stream_handle(stream, dev)))
+    return outputs
+
+
+def tl_dtg_backward(inputs, gout, gin=None, dtype="f64", stream=None):
+    """Adjoint on device tensors: gout is [39, n] or 39 arrays (None = output not in the functional).
+    Returns the [43, n] input gradients (allocated if not given)."""
+    import torch
+    code = _dtype_code(dtype)
+    td = _torch_dtype(code)
+    rows = _rows(inputs, N_IN, "inputs")
+    n = rows[0].shape[0]
+    dev = rows[0].device
+    grows = _rows(gout, N_OUT, "gout", allow_none=True)
+    if gin is None:
+        gin = torch.empty((N_IN, n), dtype=td, device=dev)
+    girows = _rows(gin, N_IN, "gin")
+    itab = _table(rows, N_IN, n, td, "cuda", "inputs")
+    gtab = _table(grows, N_OUT, n, td, "cuda", "gout")
+    gitab = _table(girows, N_IN, n, td, "cuda", "gin")
+    if n == 0:
+        _nonnull_empty(itab, N_IN)
+        _nonnull_empty(gitab, N_IN)
+    with torch.cuda.device(dev):
+        _check(lib().tl_dtg_backward(ctypes.byref(itab), ctypes.byref(gtab), ctypes.byref(gitab), n, code,
+                                     _stream_handle(stream, dev)))
+    return gin
+
+
+def tl_dtg_host_workspace_bytes(n, dtype="f64"):
+    return int(lib().tl_dtg_host_workspace_bytes(n, _dtype_code(dtype)))
+
+
+def tl_dtg_forward_host(inputs, outputs, workspace=None, dtype="f64", stream=None, device=None):
+    """Forward with HOST tensors (page-locked for full speed): the library copies inputs in, runs the
+    kernel and copies outputs back, all on `stream`.  `workspace` is a device uint8 tensor of at least
+    tl_dtg_host_workspace_bytes(n) bytes (allocated if not given).  Returns outputs; they are valid
+    after the stream is synchronised."""
+    import torch
+    code = _dtype_code(dtype)
+    td = _torch_dtype(code)
+    rows = _rows(inputs, N_IN, "inputs")
+    orows = _rows(outputs, N_OUT, "outputs")
+    n = rows[0].shape[0]
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    need = tl_dtg_host_workspace_bytes(n, code)
+    if workspace is None:
+        workspace = torch.empty(max(need, 16), dtype=torch.uint8, device=dev)
+    itab = _table(rows, N_IN, n, td, "cpu", "inputs")
+    otab = _table(orows, N_OUT, n, td, "cpu", "outputs")
+    if n == 0:
+        _nonnull_empty(itab, N_IN)
+        _nonnull_empty(otab, N_OUT)
+    with torch.cuda.device(dev):
+        _check(lib().tl_dtg_forward_host(ctypes.byref(itab), ctypes.byref(otab), n, code,
+                                         ctypes.c_void_p(workspace.data_ptr()), workspace.numel(),
+                                         _stream_handle(stream, dev)))
+    return outputs
+
+
+def _autograd():
+    import torch
+
+    class DtgFunction(torch.autograd.Function):
+        """The fused chain as a differentiable op on a [43, n] float64 tensor.  Returns
+        (ginv [6, n], gamma [18, n], dbcov [9, n], dtg [6, n]).  The backward runs the hand-written
+        adjoint kernel, which recomputes g^ij and Gamma from the saved inputs; outputs that receive no
+        gradient are passed to it as NULL and never read."""
+
+        @staticmethod
+        def forward(ctx, x, dtype="f64"):
+            n = x.shape[1]
+            dev = x.device
+            ginv = torch.empty((6, n), dtype=x.dtype, device=dev)
+            gamma = torch.empty((18, n), dtype=x.dtype, device=dev)
+            dbcov = torch.empty((9, n), dtype=x.dtype, device=dev)
+            dtg = torch.empty((6, n), dtype=x.dtype, device=dev)
+            outs = [ginv[s] for s in range(6)] + [gamma[s] for s in range(18)] + \
+                   [dbcov[s] for s in range(9)] + [dtg[s] for s in range(6)]
+            tl_dtg_forward(x, outs, dtype=dtype)
+            ctx.save_for_backward(x)
+            ctx.dtype = dtype
+            ctx.set_materialize_grads(False)
+            return ginv, gamma, dbcov, dtg
+
+        @staticmethod
+        def backward(ctx, g_ginv, g_gamma, g_dbcov, g_dtg):
+            (x,) = ctx.saved_tensors
+            gout = []
+            for g, rows in ((g_ginv, 6), (g_gamma, 18), (g_dbcov, 9), (g_dtg, 6)):
+                if g is None:
+                    gout += [None] * rows
+                else:
+                    g = g.contiguous()
+                    gout += [g[s] for s in range(rows)]
+            gin = tl_dtg_backward(x.contiguous(), gout, dtype=ctx.dtype)
+            return gin, None
+
+    return DtgFunction
+
+
+_DtgFunction = None
+
+
+def dtg(x, dtype="f64"):
+    """Differentiable fused chain: returns (ginv, gamma, dbcov, dtg) for a [43, n] device tensor."""
+    global _DtgFunction
+    if _DtgFunction is None:
+        _DtgFunction = _autograd()
+    return _DtgFunction.apply(x, dtype)
+
+
+def DtgFunction():
+    """The torch.autograd.Function class behind dtg()."""
+    global _DtgFunction
+    if _DtgFunction is None:
+        _DtgFunction = _autograd()
+    return _DtgFunction

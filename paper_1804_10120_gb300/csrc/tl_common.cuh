@@ -1,0 +1,104 @@
+// tl_common.cuh -- layout constants, argument blocks and small exact helpers shared by the kernels.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace tl {
+
+// Offsets into the 43-entry input table and the 39-entry output table (see include/tl.h).
+enum : int { IN_G = 0, IN_DG = 6, IN_K = 24, IN_ALPHA = 30, IN_BETA = 31, IN_DBETA = 34, N_IN = 43 };
+enum : int { OUT_GINV = 0, OUT_GAMMA = 6, OUT_DBCOV = 24, OUT_DTG = 33, N_OUT = 39 };
+
+// Packed position of the unordered index pair {i, j}: (00,01,02,11,12,22) -> 0..5.
+__host__ __device__ constexpr int sym(int i, int j)
+{
+    return (i <= j) ? (i * (5 - i)) / 2 + j : (j * (5 - j)) / 2 + i;
+}
+
+// Kernel argument blocks: the component pointer tables travel by value in the parameter space
+// (82 pointers = 656 bytes), so a launch needs no device-side table.
+template <typename T> struct FwdArgs {
+    const T *in[N_IN];
+    T *out[N_OUT];
+};
+template <typename T> struct BwdArgs {
+    const T *in[N_IN];
+    const T *gout[N_OUT];   // nullptr = output absent from the functional
+    T *gin[N_IN];
+};
+
+// Streaming loads and stores: each element is touched exactly once, so keep it out of L1 and mark it
+// evict-first in L2.
+template <typename T> __device__ __forceinline__ T ld_stream(const T *p) { return __ldcs(p); }
+template <typename T> __device__ __forceinline__ void st_stream(T *p, T v) { __stcs(p, v); }
+
+// ---- exact power-of-two scaling of binary64 on the integer pipe (the FP64 pipe is the scarce one) ----
+// half_exact(x) == x * 0.5 and twice_exact(x) == x * 2.0 in IEEE round-to-nearest-even for every
+// binary64 value, including zeros, subnormals, infinities and NaN.
+__device__ __forceinline__ double half_exact(double x)
+{
+    const uint64_t b = (uint64_t)__double_as_longlong(x);
+    const uint64_t sign = b & 0x8000000000000000ull, mag = b & 0x7fffffffffffffffull;
+    const uint64_t e = mag >> 52;
+    uint64_t r;
+    if (e > 1 && e < 2047)
+        r = mag - (1ull << 52);
+    else if (e == 2047)
+        r = mag;
+    else   // zero, subnormal or smallest normal: shift right, ties to even
+        r = (mag >> 1) + ((mag & 1) & ((mag >> 1) & 1));
+    return __longlong_as_double((long long)(sign | r));
+}
+
+__device__ __forceinline__ double twice_exact(double x)
+{
+    const uint64_t b = (uint64_t)__double_as_longlong(x);
+    const uint64_t sign = b & 0x8000000000000000ull, mag = b & 0x7fffffffffffffffull;
+    const uint64_t e = mag >> 52;
+    uint64_t r;
+    if (e == 0)
+        r = mag << 1;                         // subnormal (or zero): exact, may become normal
+    else if (e < 2046)
+        r = mag + (1ull << 52);
+    else if (e == 2046)
+        r = 0x7ff0000000000000ull;            // overflow to infinity
+    else
+        r = mag;                              // inf / nan
+    return __longlong_as_double((long long)(sign | r));
+}
+
+// ---- binary64 reciprocal ------------------------------------------------------------------------------
+// Seed: binary32 reciprocal (MUFU) of the binary32 truncation of d, both conversions done on integer
+// bits; relative seed error e0 < 2^-21.  One third-order Newton-Raphson step in binary64,
+//   e = 1 - d r,  r' = r + r (e + e^2),
+// leaves a relative error of about e0^3 < 2^-63 plus rounding, i.e. within one ulp.  Three FP64
+// operations instead of the division sequence.  Outside the binary32 exponent range (and for zero,
+// inf, nan) the IEEE quotient 1.0 / d is used.
+__device__ __forceinline__ double rcp_f64(double d)
+{
+    const uint64_t b = (uint64_t)__double_as_longlong(d);
+    const int e = (int)((b >> 52) & 0x7ff);
+    if (e > 1023 - 125 && e < 1023 + 125) {
+        const uint32_t fb = (uint32_t)((b >> 32) & 0x80000000u) | (uint32_t)((e - 1023 + 127) << 23) |
+                            (uint32_t)((b >> 29) & 0x7fffffu);
+        float rf;
+        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(__uint_as_float(fb)));
+        const uint32_t rb = __float_as_uint(rf);
+        const uint64_t r64 = ((uint64_t)(rb & 0x80000000u) << 32) |
+                             ((uint64_t)(((rb >> 23) & 0xff) - 127 + 1023) << 52) |
+                             ((uint64_t)(rb & 0x7fffffu) << 29);
+        const double r = __longlong_as_double((long long)r64);
+        const double err = fma(-d, r, 1.0);
+        return fma(r, fma(err, err, err), r);
+    }
+    return 1.0 / d;
+}
+
+// Grid-stride bounds for a 1-D launch.
+struct GridStride {
+    int64_t first, step;
+    __device__ __forceinline__ GridStride()
+        : first((int64_t)blockIdx.x * blockDim.x + threadIdx.x), step((int64_t)gridDim.x * blockDim.x) {}
+};
+
+}  // namespace tl

@@ -1,0 +1,24 @@
+// tl_kernels.h -- internal launchers (C++; not part of the C ABI).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+#include "tl_common.cuh"
+
+namespace tl {
+
+constexpr int kFwdThreads = 256;
+
+constexpr int kBwdThreads = 128;
+
+cudaError_t launch_fwd_f64(const FwdArgs<double> &a, int64_t n, int grid, cudaStream_t s);
+cudaError_t launch_fwd_f32(const FwdArgs<float> &a, int64_t n, int grid, cudaStream_t s);
+cudaError_t launch_fwd_ff(const FwdArgs<double> &a, int64_t n, int grid, cudaStream_t s);
+cudaError_t launch_bwd_f64(const BwdArgs<double> &a, int64_t n, int grid, cudaStream_t s);
+cudaError_t launch_bwd_ff(const BwdArgs<double> &a, int64_t n, int grid, cudaStream_t s);
+
+// Resident blocks per SM of each kernel (0 where a kernel is not provided).
+cudaError_t occupancy_fwd(int *f64, int *f32, int *ff);
+cudaError_t occupancy_bwd(int *f64, int *ff);
+cudaError_t occupancy_fwd_ff(int *ff);
+
+}  // namespace tl

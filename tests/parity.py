@@ -1,0 +1,43 @@
+"""Comparison helpers shared by the GPU parity tests (no arithmetic of the method lives here)."""
+import numpy as np
+
+# FP64 gate: per output component array, max_x |y - y_ref| <= TOL_F64 * max_x |y_ref|
+# (pointwise relative error with the array's own maximum as the floor: Gamma and nabla beta cancel to
+# ~0 at some points, where only an absolute error relative to the component's scale is meaningful).
+TOL_F64 = 1e-12
+
+OUT_NAMES = (["ginv%d" % p for p in range(6)] + ["gamma%d_%d" % (i, p) for i in range(3) for p in range(6)] +
+             ["dbcov%d%d" % (i, j) for i in range(3) for j in range(3)] + ["dtg%d" % p for p in range(6)])
+IN_NAMES = (["g%d" % p for p in range(6)] + ["dg%d_%d" % (p, k) for p in range(6) for k in range(3)] +
+            ["K%d" % p for p in range(6)] + ["alpha"] + ["beta%d" % i for i in range(3)] +
+            ["dbeta%d%d" % (i, j) for i in range(3) for j in range(3)])
+
+
+def component_errors(y, y_ref):
+    """Per-row normwise relative error max|y - y_ref| / max|y_ref| (absolute error where the row of
+    y_ref is identically zero)."""
+    y = np.asarray(y, dtype=np.float64)
+    y_ref = np.asarray(y_ref, dtype=np.float64)
+    assert y.shape == y_ref.shape
+    if y.shape[-1] == 0:
+        return np.zeros(y.shape[0])
+    diff = np.abs(y - y_ref).max(axis=1)
+    scale = np.abs(y_ref).max(axis=1)
+    return np.where(scale > 0, diff / np.where(scale > 0, scale, 1.0), diff)
+
+
+def pointwise_floor_errors(y, y_ref, floor_frac):
+    """max_x |y - y_ref| / max(|y_ref(x)|, floor_frac * max|y_ref|) per row (a stricter view)."""
+    y = np.asarray(y, dtype=np.float64)
+    y_ref = np.asarray(y_ref, dtype=np.float64)
+    scale = np.abs(y_ref).max(axis=1, keepdims=True)
+    den = np.maximum(np.abs(y_ref), floor_frac * scale)
+    den = np.where(den > 0, den, 1.0)
+    return (np.abs(y - y_ref) / den).max(axis=1)
+
+
+def assert_components(y, y_ref, tol, names=OUT_NAMES, what=""):
+    errs = component_errors(y, y_ref)
+    bad = [(names[c], float(errs[c])) for c in range(len(errs)) if not errs[c] <= tol]
+    assert not bad, "%s components over %.1e: %s" % (what, tol, bad[:8])
+    return errs

@@ -1,0 +1,92 @@
+"""The C-ABI library: it loads, exports every symbol include/tl.h declares, and its host-side argument
+checks reject bad calls before touching a device (no GPU needed; nothing is computed here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_1804_10120_gb300 import build, lib
+    build.build()
+    return lib()
+
+
+def declared_symbols():
+    syms = []
+    for name in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if name.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", name)).read()
+            syms += re.findall(r"TL_API\s+[\w\s\*]+?\b(tl_\w+)\s*\(", text)
+    return syms
+
+
+def test_exports_every_declared_symbol(L):
+    syms = declared_symbols()
+    assert "tl_dtg_forward" in syms and "tl_dtg_backward" in syms
+    for s in syms:
+        assert hasattr(L, s), s
+
+
+def test_status_strings(L):
+    for code, name in [(0, b"TL_OK"), (1, b"TL_ERR_INVALID_ARG"), (2, b"TL_ERR_ALIGNMENT"),
+                       (3, b"TL_ERR_UNSUPPORTED"), (4, b"TL_ERR_CUDA"), (5, b"TL_ERR_TIMEOUT"),
+                       (6, b"TL_ERR_PLAN_MISMATCH")]:
+        assert L.tl_status_string(code) == name
+
+
+def _tabs(base=1 << 20, n=16, esz=8, stride=None):
+    stride = stride or n * esz
+    tin = (ctypes.c_void_p * 43)(*[base + s * stride for s in range(43)])
+    tout = (ctypes.c_void_p * 39)(*[base + (43 + s) * stride for s in range(39)])
+    return tin, tout
+
+
+def test_forward_argument_checks(L):
+    tin, tout = _tabs()
+    f = L.tl_dtg_forward
+    assert f(None, ctypes.byref(tout), 16, 0, None) == 1
+    assert f(ctypes.byref(tin), ctypes.byref(tout), -1, 0, None) == 1
+    assert f(ctypes.byref(tin), ctypes.byref(tout), 16, 7, None) == 1
+    bad = (ctypes.c_void_p * 43)(*tin); bad[5] = None
+    assert f(ctypes.byref(bad), ctypes.byref(tout), 16, 0, None) == 1
+    assert b"in[5]" in L.tl_last_error()
+    mis = (ctypes.c_void_p * 43)(*tin); mis[3] = tin[3] + 4
+    assert f(ctypes.byref(mis), ctypes.byref(tout), 16, 0, None) == 2
+    # binary32 needs only 4-byte alignment, but then the 4-byte shift overlaps nothing in this layout
+    # output aliasing an input
+    alias = (ctypes.c_void_p * 39)(*tout); alias[2] = tin[7]
+    assert f(ctypes.byref(tin), ctypes.byref(alias), 16, 0, None) == 1
+    # two outputs overlapping partially
+    ov = (ctypes.c_void_p * 39)(*tout); ov[4] = tout[3] + 8
+    assert f(ctypes.byref(tin), ctypes.byref(ov), 16, 0, None) == 1
+    # inputs may overlap each other (read-only)
+    rd = (ctypes.c_void_p * 43)(*tin); rd[1] = tin[0]
+    assert f(ctypes.byref(rd), ctypes.byref(tout), 0, 0, None) == 0
+    # n == 0: nothing to do, no device touched
+    assert f(ctypes.byref(tin), ctypes.byref(tout), 0, 0, None) == 0
+
+
+def test_backward_argument_checks(L):
+    tin, tout = _tabs()
+    gout = (ctypes.c_void_p * 39)(*([None] * 39))
+    gin = (ctypes.c_void_p * 43)(*[(1 << 30) + s * 128 for s in range(43)])
+    b = L.tl_dtg_backward
+    assert b(ctypes.byref(tin), ctypes.byref(gout), ctypes.byref(gin), 0, 0, None) == 0   # NULL gouts allowed
+    assert b(ctypes.byref(tin), ctypes.byref(gout), ctypes.byref(gin), 0, 1, None) == 3   # no f32 adjoint
+    g2 = (ctypes.c_void_p * 43)(*gin); g2[0] = tin[0]
+    assert b(ctypes.byref(tin), ctypes.byref(gout), ctypes.byref(g2), 16, 0, None) == 1
+
+
+def test_host_workspace_size(L):
+    L.tl_dtg_host_workspace_bytes.restype = ctypes.c_size_t
+    L.tl_dtg_host_workspace_bytes.argtypes = [ctypes.c_int64, ctypes.c_int]
+    assert L.tl_dtg_host_workspace_bytes(0, 0) == 0
+    assert L.tl_dtg_host_workspace_bytes(100, 0) == 100 * 82 * 8
+    assert L.tl_dtg_host_workspace_bytes(100, 1) == 100 * 82 * 4
+    big = 1 << 24
+    assert L.tl_dtg_host_workspace_bytes(big, 0) == 2 * (1 << 20) * 82 * 8

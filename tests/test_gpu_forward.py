@@ -1,0 +1,154 @@
+"""GPU parity of the fused forward chain against the CPU oracle, through the C ABI.
+
+Binary64 forms are gated per output component at max|y - y_ref| <= 1e-12 * max|y_ref| (parity.py);
+the binary32-storage form at the bound derived for it (TOL_F32_* below)."""
+import numpy as np
+import pytest
+
+import gridgen
+import oracle
+from tests.parity import TOL_F64, assert_components, component_errors, OUT_NAMES
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+# Binary32 form.  Computation error alone (oracle evaluated on the binary32-rounded inputs): the chain
+# is at most ~6 dependent roundings deep (bracket 2, raise 3, covariant derivative 3, Eq. 2 2) and each
+# output is a short sum whose terms are bounded by its component's maximum, so a normwise error of a
+# few tens of ulp(2^-24 = 6e-8) bounds it: 2e-6.  End to end against the binary64 inputs the storage
+# rounding of the 43 inputs (relative 2^-24 each) enters with the same conditioning: 5e-6.
+TOL_F32_COMPUTE = 2e-6
+TOL_F32_E2E = 5e-6
+
+
+def dev():
+    return torch.device("cuda", 0)
+
+
+def run_f64(x_np, dtype="f64"):
+    import paper_1804_10120_gb300 as tl
+    x = torch.from_numpy(x_np).to(dev())
+    y = tl.tl_dtg_forward(x, dtype=dtype)
+    torch.cuda.synchronize()
+    return y.cpu().numpy()
+
+
+def test_config0_f64_all_components():
+    x = gridgen.random_grid(4096, 0)
+    y = run_f64(x)
+    y_ref = oracle.forward(x)
+    assert_components(y, y_ref, TOL_F64, what="N=4096 seed 0 f64")
+
+
+@pytest.mark.parametrize("n", [1, 2, 31, 255, 257, 4097, 100003])
+def test_ragged_sizes_f64(n):
+    x = gridgen.random_grid(n, 100 + n)
+    y = run_f64(x)
+    assert_components(y, oracle.forward(x), TOL_F64, what="n=%d" % n)
+
+
+def test_empty_grid():
+    import paper_1804_10120_gb300 as tl
+    x = torch.empty((43, 0), dtype=torch.float64, device=dev())
+    y = tl.tl_dtg_forward(x)
+    torch.cuda.synchronize()
+    assert y.shape == (39, 0)
+
+
+def test_unaligned_and_scattered_tables():
+    """Arrays that are only 8-byte aligned, each from its own allocation, with a stream that is not the
+    default one."""
+    import paper_1804_10120_gb300 as tl
+    n = 5001
+    x = gridgen.random_grid(n, 77)
+    ins = []
+    for s in range(43):
+        buf = torch.empty(n + 1, dtype=torch.float64, device=dev())
+        v = buf[1:]                        # shifted by 8 bytes
+        v.copy_(torch.from_numpy(x[s]))
+        ins.append(v)
+    outs = []
+    for s in range(39):
+        buf = torch.empty(n + 3, dtype=torch.float64, device=dev())
+        outs.append(buf[3:])
+    st = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    tl.tl_dtg_forward(ins, outs, stream=st)
+    st.synchronize()
+    y = np.stack([o.cpu().numpy() for o in outs])
+    assert_components(y, oracle.forward(x), TOL_F64, what="unaligned")
+
+
+def test_conformal_grid_exact_zeros_f64():
+    """Conformally flat metric, beta = K = 0: nabla beta and d_t g vanish exactly; Gamma matches."""
+    side = 32
+    x = gridgen.conformal_grid(side)
+    y = run_f64(x)
+    assert np.all(y[24:39] == 0.0)
+    assert_components(y, oracle.forward(x), TOL_F64, what="conformal f64")
+
+
+def test_full_size_sampled_f64():
+    """N = 2^24 (256^3), seed 1, in the launch configuration the benchmark times; the oracle checks a
+    sample of 65536 points (random, plus the first and last 1024)."""
+    import paper_1804_10120_gb300 as tl
+    n = 1 << 24
+    x = gridgen.random_grid(n, 1)
+    xd = torch.from_numpy(x).to(dev())
+    y = tl.tl_dtg_forward(xd)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(1)
+    idx = np.unique(np.concatenate([np.arange(1024), np.arange(n - 1024, n), rng.integers(0, n, 63488)]))
+    ys = y[:, torch.from_numpy(idx).to(dev())].cpu().numpy()
+    y_ref = oracle.forward(np.ascontiguousarray(x[:, idx]))
+    assert_components(ys, y_ref, TOL_F64, what="N=2^24 sampled")
+    # every output written: no NaN / untouched memory anywhere
+    assert bool(torch.isfinite(y).all())
+
+
+def test_f32_storage_form():
+    x = gridgen.random_grid(1 << 16, 4)
+    x32 = x.astype(np.float32)
+    import paper_1804_10120_gb300 as tl
+    y = tl.tl_dtg_forward(torch.from_numpy(x32).to(dev()), dtype="f32")
+    torch.cuda.synchronize()
+    y = y.cpu().numpy().astype(np.float64)
+    compute = component_errors(y, oracle.forward(x32.astype(np.float64)))
+    e2e = component_errors(y, oracle.forward(x))
+    assert compute.max() <= TOL_F32_COMPUTE, dict(zip(OUT_NAMES, compute))
+    assert e2e.max() <= TOL_F32_E2E, dict(zip(OUT_NAMES, e2e))
+
+
+def test_f32_conformal_exact_zeros():
+    side = 32
+    x = gridgen.conformal_grid(side).astype(np.float32)
+    import paper_1804_10120_gb300 as tl
+    y = tl.tl_dtg_forward(torch.from_numpy(x).to(dev()), dtype="f32")
+    torch.cuda.synchronize()
+    y = y.cpu().numpy()
+    assert np.all(y[24:39] == 0.0)
+    err = component_errors(y.astype(np.float64), oracle.forward(x.astype(np.float64)))
+    assert err.max() <= TOL_F32_COMPUTE
+
+
+def test_host_buffer_entry_point():
+    """tl_dtg_forward_host: page-locked host arrays in and out, ragged chunking (n not a multiple of the
+    pipeline chunk)."""
+    import paper_1804_10120_gb300 as tl
+    n = (1 << 20) * 2 + 12345
+    x = gridgen.random_grid(n, 8)
+    xin = torch.from_numpy(x).pin_memory()
+    yout = torch.empty((39, n), dtype=torch.float64).pin_memory()
+    tl.tl_dtg_forward_host(xin, yout)
+    torch.cuda.synchronize()
+    y = yout.numpy()
+    rng = np.random.default_rng(8)
+    idx = np.unique(np.concatenate([np.arange(2048), np.arange((1 << 20) - 1024, (1 << 20) + 1024),
+                                    np.arange(n - 2048, n), rng.integers(0, n, 20000)]))
+    assert_components(y[:, idx], oracle.forward(np.ascontiguousarray(x[:, idx])), TOL_F64, what="host path")
+
+
+def test_device_check_rejects_nothing_on_sm103():
+    import paper_1804_10120_gb300 as tl
+    assert torch.cuda.get_device_capability(0) == (10, 3)
+    assert tl.lib().tl_version() >= 10000
