@@ -1,0 +1,27 @@
+/*
+ * tl_testing.h -- test hooks of libtl (not part of the stable API).
+ *
+ * tl_testing_ff applies one float-float primitive of the TL_F64_FF kernels (pairs of binary32 values
+ * carried as hi + lo, converted to and from binary64 with integer operations) elementwise, so the
+ * primitives can be checked against exact rational arithmetic:
+ *   op 0: y[i] = merge(split(a[i]))                  (conversion round trip)
+ *   op 1: y[i] = merge(split(a[i]) - split(b[i]))     (pair subtraction)
+ *   op 2: y[i] = merge(dot3(split(a), split(b), split(c), split(d), split(e), split(f)))[i]
+ *         = a b + c d + e f                           (the contraction kernel's dot product)
+ * All pointers are DEVICE arrays of n doubles (b..f may be NULL when the op does not read them); the
+ * work is enqueued on `stream`.  Returns a tl_status code (0 = OK).
+ */
+#ifndef TL_TESTING_H
+#define TL_TESTING_H
+#include "tl.h"
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+TL_API tl_status tl_testing_ff(int op, const double *a, const double *b, const double *c, const double *d,
+                               const double *e, const double *f, double *y, int64_t n, tl_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

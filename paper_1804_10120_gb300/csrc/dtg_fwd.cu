@@ -7,108 +7,9 @@
 // kernels (one thread per point and output component, one kernel per expression, pointer tables
 // read from global memory; Sec. 4), the whole chain is one kernel and the pointer tables are kernel
 // parameters.
-#include "tl_common.cuh"
-#include "tl_kernels.h"
+#include "dtg_fwd_body.cuh"
 
 namespace tl {
-
-// The bracket of Eq. 3 for the stored pairs, T[l][p(j,k)] = d_k g_jl + d_j g_lk - d_l g_jk, from
-// D(a,b,c) = d_c g_ab.  When l is one of j, k two terms cancel identically:
-//   l == j: T = d_k g_jj;   l == k: T = d_j g_kk;   j == k != l: T = 2 d_j g_jl - d_l g_jj.
-// Only the three (j<k, l outside {j,k}) entries need the full three-term sum.
-template <typename R>
-__device__ __forceinline__ R dgc(const R (&dg)[18], int i, int j, int k) { return dg[3 * sym(i, j) + k]; }
-
-template <typename R>
-__device__ __forceinline__ void christoffel_bracket(const R (&dg)[18], R (&T)[3][6])
-{
-#define D(i_, j_, k_) dgc<R>(dg, i_, j_, k_)
-#pragma unroll
-    for (int l = 0; l < 3; ++l)
-#pragma unroll
-        for (int j = 0; j < 3; ++j)
-#pragma unroll
-            for (int k = j; k < 3; ++k) {
-                const int p = sym(j, k);
-                if (l == j)
-                    T[l][p] = D(j, j, k);
-                else if (l == k)
-                    T[l][p] = D(k, k, j);
-                else if (j == k)
-                    T[l][p] = fma((R)2, D(j, l, j), -D(j, j, l));
-                else
-                    T[l][p] = (D(j, l, k) + D(l, k, j)) - D(j, k, l);
-            }
-#undef D
-}
-
-// ------------------------------------------------------------------------------------ binary64 forward
-__device__ __forceinline__ void fwd_point_f64(const FwdArgs<double> &a, int64_t x)
-{
-    // step 1: inverse metric by cofactors; det by first-row expansion
-    const double g00 = ld_stream(a.in[IN_G + 0] + x), g01 = ld_stream(a.in[IN_G + 1] + x),
-                 g02 = ld_stream(a.in[IN_G + 2] + x), g11 = ld_stream(a.in[IN_G + 3] + x),
-                 g12 = ld_stream(a.in[IN_G + 4] + x), g22 = ld_stream(a.in[IN_G + 5] + x);
-    double dg[18];
-#pragma unroll
-    for (int s = 0; s < 18; ++s)
-        dg[s] = ld_stream(a.in[IN_DG + s] + x);
-
-    double c[6];
-    c[0] = fma(g11, g22, -(g12 * g12));
-    c[1] = fma(g02, g12, -(g01 * g22));
-    c[2] = fma(g01, g12, -(g02 * g11));
-    c[3] = fma(g00, g22, -(g02 * g02));
-    c[4] = fma(g01, g02, -(g00 * g12));
-    c[5] = fma(g00, g11, -(g01 * g01));
-    const double det = fma(g00, c[0], fma(g01, c[1], g02 * c[2]));
-    const double rdet = rcp_f64(det);
-    double ginv[6], h[6];
-#pragma unroll
-    for (int p = 0; p < 6; ++p) {
-        ginv[p] = c[p] * rdet;
-        h[p] = half_exact(ginv[p]);          // 1/2 g^il of Eq. 3
-        st_stream(a.out[OUT_GINV + p] + x, ginv[p]);
-    }
-
-    // step 2: Christoffel symbols, Eq. 3
-    double T[3][6];
-    christoffel_bracket<double>(dg, T);
-    double gam[3][6];
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int p = 0; p < 6; ++p) {
-            gam[i][p] = fma(h[sym(i, 2)], T[2][p], fma(h[sym(i, 1)], T[1][p], h[sym(i, 0)] * T[0][p]));
-            st_stream(a.out[OUT_GAMMA + 6 * i + p] + x, gam[i][p]);
-        }
-
-    // step 3: nabla_j beta_i = d_j beta_i - Gamma^k_ij beta_k
-    const double b0 = ld_stream(a.in[IN_BETA + 0] + x), b1 = ld_stream(a.in[IN_BETA + 1] + x),
-                 b2 = ld_stream(a.in[IN_BETA + 2] + x);
-    double nb[3][3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            const int p = sym(i, j);
-            const double B = ld_stream(a.in[IN_DBETA + 3 * i + j] + x);
-            nb[i][j] = fma(-gam[2][p], b2, fma(-gam[1][p], b1, fma(-gam[0][p], b0, B)));
-            st_stream(a.out[OUT_DBCOV + 3 * i + j] + x, nb[i][j]);
-        }
-
-    // step 4: Eq. 2, d_t g_ij = -2 alpha K_ij + nabla_i beta_j + nabla_j beta_i
-    const double m2a = -twice_exact(ld_stream(a.in[IN_ALPHA] + x));
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = i; j < 3; ++j) {
-            const int p = sym(i, j);
-            const double K = ld_stream(a.in[IN_K + p] + x);
-            const double s = (i == j) ? twice_exact(nb[i][i]) : nb[i][j] + nb[j][i];
-            st_stream(a.out[OUT_DTG + p] + x, fma(m2a, K, s));
-        }
-}
 
 __global__ void __launch_bounds__(kFwdThreads) dtg_fwd_f64_kernel(const FwdArgs<double> a, int64_t n)
 {

@@ -152,3 +152,71 @@ def test_device_check_rejects_nothing_on_sm103():
     import paper_1804_10120_gb300 as tl
     assert torch.cuda.get_device_capability(0) == (10, 3)
     assert tl.lib().tl_version() >= 10000
+
+
+# --------------------------------------------------------------------------- float-float contractions
+
+def test_ff_config0_all_components():
+    x = gridgen.random_grid(4096, 0)
+    y = run_f64(x, dtype="f64_ff")
+    assert_components(y, oracle.forward(x), TOL_F64, what="N=4096 seed 0 f64_ff")
+
+
+@pytest.mark.parametrize("n", [1, 33, 4099, 100003])
+def test_ff_ragged_sizes(n):
+    x = gridgen.random_grid(n, 200 + n)
+    assert_components(run_f64(x, dtype="f64_ff"), oracle.forward(x), TOL_F64, what="ff n=%d" % n)
+
+
+def test_ff_full_size_sampled():
+    import paper_1804_10120_gb300 as tl
+    n = 1 << 24
+    x = gridgen.random_grid(n, 1)
+    y = tl.tl_dtg_forward(torch.from_numpy(x).to(dev()), dtype="f64_ff")
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(11)
+    idx = np.unique(np.concatenate([np.arange(1024), np.arange(n - 1024, n), rng.integers(0, n, 63488)]))
+    ys = y[:, torch.from_numpy(idx).to(dev())].cpu().numpy()
+    assert_components(ys, oracle.forward(np.ascontiguousarray(x[:, idx])), TOL_F64, what="ff N=2^24 sampled")
+    assert bool(torch.isfinite(y).all())
+
+
+def test_ff_exact_zero_cases():
+    """Flat metric (Gamma = 0), conformal grid with beta = K = 0 (nabla beta = d_t g = 0): exact zeros
+    survive the pair arithmetic."""
+    x = gridgen.conformal_grid(24)
+    y = run_f64(x, dtype="f64_ff")
+    assert np.all(y[24:39] == 0.0)
+    assert_components(y, oracle.forward(x), TOL_F64, what="ff conformal")
+    x = gridgen.random_grid(777, 31)
+    x[0:6] = np.array([1, 0, 0, 1, 0, 1.0])[:, None]
+    x[6:24] = 0.0
+    y = run_f64(x, dtype="f64_ff")
+    assert np.all(y[6:24] == 0.0)
+    assert np.array_equal(y[24:33], x[34:43])
+
+
+def test_ff_extreme_values_and_fallback():
+    """Values the pair format cannot carry (|x| >= 2^63, inf) send their point through the all-binary64
+    evaluation; tiny, subnormal, power-of-two and negative-zero values go through the pairs."""
+    n = 4096
+    x = gridgen.random_grid(n, 41)
+    x[31, 0:8] = 2.0 ** 70                 # huge shift: fallback path
+    x[34, 8:16] = -3.0e30                  # huge d_j beta_i (below 2^127 but above 2^63): fallback
+    x[6 + 5, 16:24] = 1e300                # huge metric derivative: fallback
+    x[31:34, 24:32] = 1e-40                # tiny shift (no lo part)
+    x[34:43, 32:40] = 5e-324               # subnormal d beta
+    x[6:24, 40:48] = 2.0 ** -30            # powers of two in the bracket
+    x[0:6, 48:56] = np.array([2.0, 0, 0, 4.0, 0, 8.0])[:, None]   # diagonal powers of two: exact inverse
+    x[31:34, 56:64] = -0.0
+    y = run_f64(x, dtype="f64_ff")
+    y_ref = oracle.forward(x)
+    # huge values make the per-component maxima huge; check the extreme rows pointwise in their own
+    # scale and the rest of the grid with the standard gate
+    for lo, hi in [(0, 8), (8, 16), (16, 24)]:
+        assert_components(y[:, lo:hi], y_ref[:, lo:hi], TOL_F64, what="fallback rows %d-%d" % (lo, hi))
+    assert_components(y[:, 24:], y_ref[:, 24:], TOL_F64, what="tiny/pow2 rows")
+    x[31, 64:72] = np.inf
+    y = run_f64(x[:, 64:72].copy(), dtype="f64_ff")
+    y_ref = oracle.forward(x[:, 64:72].copy())
+    assert np.array_equal(np.isnan(y), np.isnan(y_ref)) and np.array_equal(np.isinf(y), np.isinf(y_ref))
