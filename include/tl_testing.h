@@ -4,7 +4,7 @@
  * tl_testing_ff applies one float-float primitive of the TL_F64_FF kernels (pairs of binary32 values
  * carried as hi + lo, converted to and from binary64 with integer operations) elementwise, so the
  * primitives can be checked against exact rational arithmetic:
- *   op 0: y[i] = merge(split(a[i]))                  (conversion round trip)
+ *   op 0: y[i] = merge(normalize(split(a[i])))       (conversion round trip)
  *   op 1: y[i] = merge(split(a[i]) - split(b[i]))     (pair subtraction)
  *   op 2: y[i] = merge(dot3(split(a), split(b), split(c), split(d), split(e), split(f)))[i]
  *         = a b + c d + e f                           (the contraction kernel's dot product)

@@ -139,7 +139,7 @@ __global__ void ff_testing_kernel(int op, const double *a, const double *b, cons
     for (int64_t i = gs.first; i < n; i += gs.step) {
         uint32_t big = 0;
         if (op == 0) {
-            y[i] = merge_ff(split_ff(a[i], big));
+            y[i] = merge_ff(normalize_ff(split_ff(a[i], big)));
         } else if (op == 1) {
             const ff pa = split_ff(a[i], big), pb = split_ff(b[i], big);
             y[i] = merge_ff(sub_ff(pa, pb));

@@ -65,7 +65,7 @@ __device__ __forceinline__ uint32_t out_of_ff_range(double x)
 }
 
 // hi + lo -> binary64 (truncated below the 53rd bit; error < 1 ulp).  Requires a normalised pair,
-// |lo| <= ulp(hi)/2, as produced by two_sum / fast_two_sum.
+// |lo| <= ulp(hi)/2, as produced by two_sum.
 __device__ __forceinline__ double merge_ff(ff v)
 {
     const uint32_t hb = __float_as_uint(v.hi), lb = __float_as_uint(v.lo);
@@ -117,8 +117,10 @@ __device__ __forceinline__ ff dot3_ff(const ff &a0, const ff &b0, const ff &a1, 
     two_sum(p0, p1, s, t0);
     two_sum(s, p2, s, t1);
     const float lo = __fadd_rn(__fadd_rn(__fadd_rn(q0, q1), __fadd_rn(q2, t0)), t1);
+    // TwoSum rather than the cheaper FastTwoSum: when the leading products cancel, |lo| may exceed
+    // |s|, and merge_ff needs |lo| <= ulp(hi) / 2, which TwoSum guarantees for any inputs.
     ff r;
-    fast_two_sum(s, lo, r.hi, r.lo);
+    two_sum(s, lo, r.hi, r.lo);
     return r;
 }
 
@@ -129,7 +131,15 @@ __device__ __forceinline__ ff sub_ff(const ff &a, const ff &b)
     two_sum(a.hi, -b.hi, s, t);
     const float lo = __fadd_rn(t, __fsub_rn(a.lo, b.lo));
     ff r;
-    fast_two_sum(s, lo, r.hi, r.lo);
+    two_sum(s, lo, r.hi, r.lo);
+    return r;
+}
+
+// A pair with |lo| <= ulp(hi) / 2 (split_ff's pairs may have |lo| up to ulp(hi)).
+__device__ __forceinline__ ff normalize_ff(const ff &a)
+{
+    ff r;
+    two_sum(a.hi, a.lo, r.hi, r.lo);
     return r;
 }
 

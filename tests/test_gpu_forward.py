@@ -193,7 +193,8 @@ def test_ff_exact_zero_cases():
     x[6:24] = 0.0
     y = run_f64(x, dtype="f64_ff")
     assert np.all(y[6:24] == 0.0)
-    assert np.array_equal(y[24:33], x[34:43])
+    # d_j beta_i passes through a pair (48 significant bits): equal within the gate, not bitwise
+    assert_components(y, oracle.forward(x), TOL_F64, what="ff flat")
 
 
 def test_ff_extreme_values_and_fallback():
