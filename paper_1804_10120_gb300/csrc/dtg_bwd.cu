@@ -1,16 +1,237 @@
-// dtg_bwd.cu -- adjoint of the fused chain.
-#include "tl_common.cuh"
+// dtg_bwd.cu -- adjoint of the fused chain: given upstream gradients of the 39 outputs, the gradient of
+// L = sum gout * out with respect to the 43 stored inputs.  The paper has no adjoint; this is the
+// reverse-mode derivative of Eq. 2, the footnote to Listing 1, Eq. 3 and the inverse metric, taken in
+// reverse order.  g^ij, the bracket T of Eq. 3 and Gamma are recomputed in registers from the inputs
+// (never stored or re-read), so one launch reads 43 inputs plus the upstream gradients present and
+// writes 43 input gradients.
+//
+// Per point, with h = g^ij / 2, Gamma^i_p = sum_l h_il T_lp, Nbar the gradient of nabla_j beta_i:
+//   Kbar_p = -2 alpha W_p,  abar = -2 sum_p K_p W_p,  Nbar_ij = U_ij + (W_p(ij), doubled on the diagonal)
+//   dbetabar_ij = Nbar_ij,  S_p = Nbar_ij + Nbar_ji (i<j) or Nbar_ii,  betabar_k = -sum_p S_p Gamma^k_p
+//   Gammabar_kp = V_kp - beta_k S_p
+//   Hbar_il = 1/2 sum_p Gammabar_ip T_lp (+ the g^ij upstream gradient on the stored entries)
+//   Tbar_lp = sum_i h_il Gammabar_ip, scattered through the bracket's three terms onto d_k g_ij
+//   gbar_ij (i<j) = -(H A H)_ij, gbar_ii = -(H A H)_ii / 2 with A = Hbar + Hbar^T   (from dH = -H dG H)
+// where W, V, U are the upstream gradients of d_t g, Gamma and nabla beta.
+#include "dtg_fwd_body.cuh"
 #include "tl_kernels.h"
 
 namespace tl {
 
-cudaError_t launch_bwd_f64(const BwdArgs<double> &, int64_t, int, cudaStream_t) { return cudaErrorNotSupported; }
+template <typename T> __device__ __forceinline__ T ld_opt(const T *p, int64_t x)
+{
+    return p ? ld_stream(p + x) : T(0);
+}
+
+// kU: upstream gradient of nabla beta present; kG: upstream gradient of g^ij present.
+template <bool kU, bool kG> __device__ __forceinline__ void bwd_point_f64(const BwdArgs<double> &a, int64_t x)
+{
+    // ---- recompute: inverse metric, bracket, Christoffel symbols
+    const double g00 = ld_stream(a.in[IN_G + 0] + x), g01 = ld_stream(a.in[IN_G + 1] + x),
+                 g02 = ld_stream(a.in[IN_G + 2] + x), g11 = ld_stream(a.in[IN_G + 3] + x),
+                 g12 = ld_stream(a.in[IN_G + 4] + x), g22 = ld_stream(a.in[IN_G + 5] + x);
+    double dg[18];
+#pragma unroll
+    for (int s = 0; s < 18; ++s)
+        dg[s] = ld_stream(a.in[IN_DG + s] + x);
+    double H[6], h[6];
+    {
+        double c[6];
+        c[0] = fma(g11, g22, -(g12 * g12));
+        c[1] = fma(g02, g12, -(g01 * g22));
+        c[2] = fma(g01, g12, -(g02 * g11));
+        c[3] = fma(g00, g22, -(g02 * g02));
+        c[4] = fma(g01, g02, -(g00 * g12));
+        c[5] = fma(g00, g11, -(g01 * g01));
+        const double det = fma(g00, c[0], fma(g01, c[1], g02 * c[2]));
+        const double rdet = rcp_f64(det);
+#pragma unroll
+        for (int p = 0; p < 6; ++p) {
+            H[p] = c[p] * rdet;
+            h[p] = half_exact(H[p]);
+        }
+    }
+    double T[3][6];
+    christoffel_bracket<double>(dg, T);
+    double gam[3][6];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int p = 0; p < 6; ++p)
+            gam[i][p] = fma(h[sym(i, 2)], T[2][p], fma(h[sym(i, 1)], T[1][p], h[sym(i, 0)] * T[0][p]));
+
+    // ---- Eq. 2
+    const double alpha = ld_stream(a.in[IN_ALPHA] + x);
+    const double m2a = -twice_exact(alpha);
+    double W[6];
+    double asum = 0.0;
+#pragma unroll
+    for (int p = 0; p < 6; ++p) {
+        W[p] = ld_opt(a.gout[OUT_DTG + p], x);
+        const double K = ld_stream(a.in[IN_K + p] + x);
+        st_stream(a.gin[IN_K + p] + x, m2a * W[p]);
+        asum = (p == 0) ? K * W[p] : fma(K, W[p], asum);
+    }
+    st_stream(a.gin[IN_ALPHA] + x, -twice_exact(asum));
+
+    // ---- covariant derivative of the shift: Nbar = dbetabar, S (symmetric fold of Nbar)
+    double S[6];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const int p = sym(i, j);
+            double nbar = (i == j) ? twice_exact(W[p]) : W[p];
+            if (kU)
+                nbar += ld_opt(a.gout[OUT_DBCOV + 3 * i + j], x);
+            st_stream(a.gin[IN_DBETA + 3 * i + j] + x, nbar);
+            if (kU) {
+                if (i == j)
+                    S[p] = nbar;
+                else if (i < j)
+                    S[p] = nbar;
+                else
+                    S[p] += nbar;
+            }
+        }
+    if (!kU) {
+#pragma unroll
+        for (int p = 0; p < 6; ++p)
+            S[p] = twice_exact(W[p]);
+    }
+    double beta[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        beta[k] = ld_stream(a.in[IN_BETA + k] + x);
+        double s = gam[k][0] * S[0];
+#pragma unroll
+        for (int p = 1; p < 6; ++p)
+            s = fma(gam[k][p], S[p], s);
+        st_stream(a.gin[IN_BETA + k] + x, -s);
+    }
+
+    // ---- Gamma: Gammabar = V - beta_k S_p
+    double gbar[3][6];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int p = 0; p < 6; ++p)
+            gbar[k][p] = fma(-beta[k], S[p], ld_opt(a.gout[OUT_GAMMA + 6 * k + p], x));
+
+    // ---- Eq. 3: Hbar (not symmetric) and Tbar
+    double Hb[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int l = 0; l < 3; ++l) {
+            double s = gbar[i][0] * T[l][0];
+#pragma unroll
+            for (int p = 1; p < 6; ++p)
+                s = fma(gbar[i][p], T[l][p], s);
+            Hb[i][l] = half_exact(s);
+        }
+    double Tb[3][6];
+#pragma unroll
+    for (int l = 0; l < 3; ++l)
+#pragma unroll
+        for (int p = 0; p < 6; ++p)
+            Tb[l][p] = fma(h[sym(2, l)], gbar[2][p], fma(h[sym(1, l)], gbar[1][p], h[sym(0, l)] * gbar[0][p]));
+
+    // ---- bracket -> d_k g_ij: every T_lp term of Eq. 3 scattered onto the stored derivative it reads
+    double dgb[18];
+#pragma unroll
+    for (int s = 0; s < 18; ++s)
+        dgb[s] = 0.0;
+#pragma unroll
+    for (int l = 0; l < 3; ++l)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+            for (int k = j; k < 3; ++k) {
+                const double t = Tb[l][sym(j, k)];
+                if (l == j) {                       // T = d_k g_jj
+                    dgb[3 * sym(j, j) + k] += t;
+                } else if (l == k) {                // T = d_j g_kk
+                    dgb[3 * sym(k, k) + j] += t;
+                } else if (j == k) {                // T = 2 d_j g_jl - d_l g_jj
+                    dgb[3 * sym(j, l) + j] += twice_exact(t);
+                    dgb[3 * sym(j, j) + l] -= t;
+                } else {                            // T = d_k g_jl + d_j g_lk - d_l g_jk
+                    dgb[3 * sym(j, l) + k] += t;
+                    dgb[3 * sym(l, k) + j] += t;
+                    dgb[3 * sym(j, k) + l] -= t;
+                }
+            }
+#pragma unroll
+    for (int s = 0; s < 18; ++s)
+        st_stream(a.gin[IN_DG + s] + x, dgb[s]);
+
+    // ---- inverse: gbar = fold of -H Hbar H onto the stored pairs, via A = Hbar + Hbar^T
+    double A[6];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = i; j < 3; ++j) {
+            double v = (i == j) ? twice_exact(Hb[i][i]) : Hb[i][j] + Hb[j][i];
+            if (kG) {
+                const double wg = ld_opt(a.gout[OUT_GINV + sym(i, j)], x);
+                v += (i == j) ? twice_exact(wg) : wg;   // the stored g^ij entry enters Hbar once
+            }
+            A[sym(i, j)] = v;
+        }
+    double M[3][3];                                   // M = H A
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            M[i][j] = fma(H[sym(i, 2)], A[sym(2, j)], fma(H[sym(i, 1)], A[sym(1, j)], H[sym(i, 0)] * A[sym(0, j)]));
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = i; j < 3; ++j) {
+            const double v = fma(M[i][2], H[sym(2, j)], fma(M[i][1], H[sym(1, j)], M[i][0] * H[sym(0, j)]));
+            st_stream(a.gin[IN_G + sym(i, j)] + x, (i == j) ? -half_exact(v) : -v);
+        }
+}
+
+template <bool kU, bool kG>
+__global__ void __launch_bounds__(kBwdThreads) dtg_bwd_f64_kernel(const BwdArgs<double> a, int64_t n)
+{
+    const GridStride gs;
+    for (int64_t x = gs.first; x < n; x += gs.step)
+        bwd_point_f64<kU, kG>(a, x);
+}
+
+static bool any_present(const double *const *p, int count)
+{
+    for (int i = 0; i < count; ++i)
+        if (p[i])
+            return true;
+    return false;
+}
+
+// The upstream gradients of nabla beta and g^ij are often absent altogether; kernels specialised on
+// their presence skip that work.  Within a group, NULL entries read as zero.
+cudaError_t launch_bwd_f64(const BwdArgs<double> &a, int64_t n, int grid, cudaStream_t s)
+{
+    const bool hasU = any_present(a.gout + OUT_DBCOV, 9), hasG = any_present(a.gout + OUT_GINV, 6);
+    if (hasU && hasG)
+        dtg_bwd_f64_kernel<true, true><<<grid, kBwdThreads, 0, s>>>(a, n);
+    else if (hasU)
+        dtg_bwd_f64_kernel<true, false><<<grid, kBwdThreads, 0, s>>>(a, n);
+    else if (hasG)
+        dtg_bwd_f64_kernel<false, true><<<grid, kBwdThreads, 0, s>>>(a, n);
+    else
+        dtg_bwd_f64_kernel<false, false><<<grid, kBwdThreads, 0, s>>>(a, n);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_bwd_ff(const BwdArgs<double> &, int64_t, int, cudaStream_t) { return cudaErrorNotSupported; }
+
 cudaError_t occupancy_bwd(int *f64, int *ff)
 {
-    *f64 = 0;
     *ff = 0;
-    return cudaSuccess;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(f64, dtg_bwd_f64_kernel<true, true>, kBwdThreads, 0);
 }
 
 }  // namespace tl

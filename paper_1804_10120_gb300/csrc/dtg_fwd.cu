@@ -21,11 +21,29 @@ __global__ void __launch_bounds__(kFwdThreads) dtg_fwd_f64_kernel(const FwdArgs<
 // ------------------------------------------------------------------------------------ binary32 forward
 // Storage and arithmetic in binary32, except det(g) and the 3x3 inverse, which are formed in binary64
 // from the (exactly widened) binary32 metric and rounded once to binary32.
-__device__ __forceinline__ void fwd_point_f32(const FwdArgs<float> &a, int64_t x)
+template <bool kIntConv>
+__device__ __forceinline__ double widen(float f, uint32_t &rare)
 {
-    const double g00 = (double)ld_stream(a.in[IN_G + 0] + x), g01 = (double)ld_stream(a.in[IN_G + 1] + x),
-                 g02 = (double)ld_stream(a.in[IN_G + 2] + x), g11 = (double)ld_stream(a.in[IN_G + 3] + x),
-                 g12 = (double)ld_stream(a.in[IN_G + 4] + x), g22 = (double)ld_stream(a.in[IN_G + 5] + x);
+    return kIntConv ? f32_to_f64(f, rare) : (double)f;
+}
+template <bool kIntConv>
+__device__ __forceinline__ float narrow(double d, uint32_t &rare)
+{
+    return kIntConv ? f64_to_f32(d, rare) : (float)d;
+}
+
+// kIntConv: binary32 <-> binary64 conversions on the integer pipe (returns false, having written nothing,
+// when an operand needs the general conversions); otherwise the compiler's F2F conversions.
+template <bool kIntConv>
+__device__ __forceinline__ bool fwd_point_f32(const FwdArgs<float> &a, int64_t x)
+{
+    uint32_t rare = 0;
+    const double g00 = widen<kIntConv>(ld_stream(a.in[IN_G + 0] + x), rare),
+                 g01 = widen<kIntConv>(ld_stream(a.in[IN_G + 1] + x), rare),
+                 g02 = widen<kIntConv>(ld_stream(a.in[IN_G + 2] + x), rare),
+                 g11 = widen<kIntConv>(ld_stream(a.in[IN_G + 3] + x), rare),
+                 g12 = widen<kIntConv>(ld_stream(a.in[IN_G + 4] + x), rare),
+                 g22 = widen<kIntConv>(ld_stream(a.in[IN_G + 5] + x), rare);
     float dg[18];
 #pragma unroll
     for (int s = 0; s < 18; ++s)
@@ -39,13 +57,17 @@ __device__ __forceinline__ void fwd_point_f32(const FwdArgs<float> &a, int64_t x
     c[5] = fma(g00, g11, -(g01 * g01));
     const double det = fma(g00, c[0], fma(g01, c[1], g02 * c[2]));
     const double rdet = rcp_f64(det);
-    float h[6];
+    float h[6], gi[6];
 #pragma unroll
     for (int p = 0; p < 6; ++p) {
-        const float gi = (float)(c[p] * rdet);
-        h[p] = 0.5f * gi;
-        st_stream(a.out[OUT_GINV + p] + x, gi);
+        gi[p] = narrow<kIntConv>(c[p] * rdet, rare);
+        h[p] = 0.5f * gi[p];
     }
+    if (kIntConv && rare)
+        return false;
+#pragma unroll
+    for (int p = 0; p < 6; ++p)
+        st_stream(a.out[OUT_GINV + p] + x, gi[p]);
     float T[3][6];
     christoffel_bracket<float>(dg, T);
     float gam[3][6];
@@ -78,13 +100,18 @@ __device__ __forceinline__ void fwd_point_f32(const FwdArgs<float> &a, int64_t x
             const float s = (i == j) ? 2.0f * nb[i][i] : nb[i][j] + nb[j][i];
             st_stream(a.out[OUT_DTG + p] + x, fmaf(m2a, K, s));
         }
+    return true;
 }
+
+// The general-conversion evaluation of one point, out of line (rare operands only).
+__device__ __noinline__ void fwd_point_f32_general(const FwdArgs<float> &a, int64_t x) { fwd_point_f32<false>(a, x); }
 
 __global__ void __launch_bounds__(kFwdThreads) dtg_fwd_f32_kernel(const FwdArgs<float> a, int64_t n)
 {
     const GridStride gs;
     for (int64_t x = gs.first; x < n; x += gs.step)
-        fwd_point_f32(a, x);
+        if (!fwd_point_f32<true>(a, x))
+            fwd_point_f32_general(a, x);
 }
 
 // ------------------------------------------------------------------------------------------- launchers

@@ -82,14 +82,17 @@ __device__ __forceinline__ void fwd_point_ff(const FwdArgs<double> &a, int64_t x
             st_stream(a.out[OUT_GAMMA + 6 * i + p] + x, merge_ff(gam[i][p]));
         }
 
-    // step 3: S_ij = Gamma^k_ij beta_k (symmetric in ij) in pairs, nabla_j beta_i = d_j beta_i - S_ij
+    // step 3: S_ij = Gamma^k_ij beta_k (symmetric in ij: 6 sums) in pairs, nabla_j beta_i = d_j beta_i - S_ij
+    ff S6[6];
+#pragma unroll
+    for (int p = 0; p < 6; ++p)
+        S6[p] = dot3_ff(gam[0][p], bf0, gam[1][p], bf1, gam[2][p], bf2);
     double nb[3][3];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
-            const int p = sym(i, j);
-            const ff S = dot3_ff(gam[0][p], bf0, gam[1][p], bf1, gam[2][p], bf2);
+            const ff &S = S6[sym(i, j)];
             uint32_t unused = 0;
             const ff B = split_ff(Bd[3 * i + j], unused);
             nb[i][j] = merge_ff(sub_ff(B, S));

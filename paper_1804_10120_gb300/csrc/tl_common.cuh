@@ -67,6 +67,40 @@ __device__ __forceinline__ double twice_exact(double x)
     return __longlong_as_double((long long)(sign | r));
 }
 
+// Out-of-line IEEE quotient for the rare operands outside the binary32 exponent range, kept out of the
+// hot path so that the compiler cannot predicate the division sequence into every point.
+static __device__ __noinline__ double rcp_f64_slow(double d) { return 1.0 / d; }
+
+// ---- exact binary32 <-> binary64 conversions on the integer pipe ------------------------------------
+// F2F conversions issue on the FP64 pipe, which runs at 1/64 of the FP32 rate on this part, so the hot
+// paths re-pack the bits instead.  Zeros are handled inline; other operands outside the normal range
+// (subnormals, inf, nan, binary32 overflow or underflow) set `rare`, and the caller then evaluates the
+// whole point through an out-of-line path that uses the compiler's conversions.
+
+// Exact widening.
+__device__ __forceinline__ double f32_to_f64(float f, uint32_t &rare)
+{
+    const uint32_t b = __float_as_uint(f);
+    const uint32_t mag = b & 0x7fffffffu;
+    rare |= (mag != 0u && mag - 0x00800000u >= 0x7f000000u) ? 1u : 0u;
+    const uint32_t hw = (mag == 0u) ? (b & 0x80000000u) : ((b & 0x80000000u) | ((mag >> 3) + (896u << 20)));
+    return __hiloint2double((int)hw, (int)(b << 29));
+}
+
+// Round-to-nearest-even narrowing.
+__device__ __forceinline__ float f64_to_f32(double d, uint32_t &rare)
+{
+    const uint32_t hw = (uint32_t)__double2hiint(d), lw = (uint32_t)__double2loint(d);
+    const uint32_t E = (hw >> 20) & 0x7ffu;
+    const bool zero = ((hw & 0x7fffffffu) | lw) == 0u;
+    rare |= (!zero && E - 897u >= 254u) ? 1u : 0u;
+    const uint32_t t = __funnelshift_l(lw, hw, 3);                    // exponent low bits | 23 fraction bits
+    const uint32_t rb = (lw >> 28) & 1u, sticky = lw & 0x0fffffffu;   // round bit, bits below it
+    const uint32_t inc = rb & ((sticky != 0u) | (t & 1u));
+    const uint32_t r = ((t - 0xC0000000u) & 0x7fffffffu) + inc;       // a carry rounds into the exponent
+    return __uint_as_float((zero ? 0u : r) | (hw & 0x80000000u));
+}
+
 // ---- binary64 reciprocal ------------------------------------------------------------------------------
 // Seed: binary32 reciprocal (MUFU) of the binary32 truncation of d, both conversions done on integer
 // bits; relative seed error e0 < 2^-21.  One third-order Newton-Raphson step in binary64,
@@ -91,7 +125,7 @@ __device__ __forceinline__ double rcp_f64(double d)
         const double err = fma(-d, r, 1.0);
         return fma(r, fma(err, err, err), r);
     }
-    return 1.0 / d;
+    return rcp_f64_slow(d);
 }
 
 // Grid-stride bounds for a 1-D launch.

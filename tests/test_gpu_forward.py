@@ -221,3 +221,17 @@ def test_ff_extreme_values_and_fallback():
     y = run_f64(x[:, 64:72].copy(), dtype="f64_ff")
     y_ref = oracle.forward(x[:, 64:72].copy())
     assert np.array_equal(np.isnan(y), np.isnan(y_ref)) and np.array_equal(np.isinf(y), np.isinf(y_ref))
+
+
+def test_f32_rare_operands_take_general_conversions():
+    """Subnormal binary32 metric entries (outside the integer fast conversion's range) are evaluated by
+    the out-of-line general path and still match."""
+    x = gridgen.random_grid(2048, 43).astype(np.float32)
+    x[1, 0:64] = np.float32(1e-40)        # subnormal g_01
+    x[2, 64:128] = np.float32(0.0)
+    x[2, 128:192] = np.float32(-0.0)
+    import paper_1804_10120_gb300 as tl
+    y = tl.tl_dtg_forward(torch.from_numpy(x).to(dev()), dtype="f32")
+    torch.cuda.synchronize()
+    err = component_errors(y.cpu().numpy().astype(np.float64), oracle.forward(x.astype(np.float64)))
+    assert err.max() <= TOL_F32_COMPUTE
