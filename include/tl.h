@@ -107,6 +107,39 @@ TL_API size_t tl_dtg_host_workspace_bytes(int64_t n, tl_dtype dtype);
 TL_API tl_status tl_dtg_forward_host(const tl_dtg_in *in, const tl_dtg_out *out, int64_t n, tl_dtype dtype,
                               void *workspace, size_t workspace_bytes, tl_stream stream);
 
+/*
+ * Batched forward over many grids (multi-domain subgrids of uneven size) in ONE persistent launch.
+ *
+ * tl_dtg_batched_prepare runs on the host, is not capturable, and may synchronise: it validates the G
+ * grids' tables (in[d], out[d], n[d] for d < G; grids may have n[d] == 0; no written array may overlap
+ * any other array of any grid), allocates and fills the plan's device-side data -- the G x 82 pointer
+ * tables (uploaded once, cf. the paper's cached GPUPointers, Sec. 4), the tile prefix sums and a status
+ * word -- and takes the launch configuration from the tuning cache when it holds an entry for this GPU,
+ * dtype and batch shape (otherwise 256 threads and full occupancy).  The plan belongs to the device
+ * current at prepare time; `in`, `out` and `n` are host arrays that the plan does not keep.
+ *
+ * tl_dtg_batched enqueues the single launch on `stream`; it allocates nothing, does not synchronise, and
+ * may be captured in a CUDA graph.  A plan may be launched any number of times; the arrays it points to
+ * must stay alive.  Calling it with another device current returns TL_ERR_PLAN_MISMATCH.
+ *
+ * tl_dtg_batched_tune times the candidate configurations (threads per block 128/256/512 x resident blocks
+ * per SM) by launching the plan on `stream` (so it writes the outputs), keeps the fastest in the plan and
+ * records it in the tuning cache: the file named by TL_TUNE_CACHE, else $HOME/.cache/tl_dtg_tune.txt
+ * (TL_TUNE_CACHE=off disables the cache).  It synchronises `stream`.
+ *
+ * tl_batch_plan_check synchronises the plan's device and returns the status word recorded by its
+ * launches (TL_OK, or TL_ERR_PLAN_MISMATCH if a launch found the plan inconsistent), then clears it.
+ */
+typedef struct tl_batch_plan tl_batch_plan;
+TL_API tl_status tl_dtg_batched_prepare(const tl_dtg_in *in, const tl_dtg_out *out, const int64_t *n, int32_t G,
+                                        tl_dtype dtype, tl_batch_plan **plan);
+TL_API tl_status tl_dtg_batched(const tl_batch_plan *plan, tl_stream stream);
+TL_API tl_status tl_dtg_batched_tune(tl_batch_plan *plan, tl_stream stream);
+TL_API tl_status tl_batch_plan_config(const tl_batch_plan *plan, int32_t *threads, int32_t *blocks_per_sm);
+TL_API tl_status tl_batch_plan_set_config(tl_batch_plan *plan, int32_t threads, int32_t blocks_per_sm);
+TL_API tl_status tl_batch_plan_check(const tl_batch_plan *plan);
+TL_API void tl_batch_plan_destroy(tl_batch_plan *plan);
+
 TL_API const char *tl_status_string(tl_status s);
 TL_API const char *tl_last_error(void);
 /* Library version as MAJOR*10000 + MINOR*100 + PATCH. */

@@ -261,3 +261,115 @@ def DtgFunction():
     if _DtgFunction is None:
         _DtgFunction = _autograd()
     return _DtgFunction
+
+
+# ------------------------------------------------------------------------------------------- batched
+
+def _batch_lib():
+    L = lib()
+    if not getattr(L, "_batch_ready", False):
+        vp, i32 = ctypes.c_void_p, ctypes.c_int32
+        L.tl_dtg_batched_prepare.argtypes = [vp, vp, vp, i32, ctypes.c_int, ctypes.POINTER(vp)]
+        L.tl_dtg_batched.argtypes = [vp, vp]
+        L.tl_dtg_batched_tune.argtypes = [vp, vp]
+        L.tl_batch_plan_config.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]
+        L.tl_batch_plan_set_config.argtypes = [vp, i32, i32]
+        L.tl_batch_plan_check.argtypes = [vp]
+        L.tl_batch_plan_destroy.argtypes = [vp]
+        L.tl_batch_plan_destroy.restype = None
+        for f in (L.tl_dtg_batched_prepare, L.tl_dtg_batched, L.tl_dtg_batched_tune, L.tl_batch_plan_config,
+                  L.tl_batch_plan_set_config, L.tl_batch_plan_check):
+            f.restype = ctypes.c_int
+        L._batch_ready = True
+    return L
+
+
+class BatchPlan:
+    """A batch plan over G grids (tl_dtg_batched_prepare).  The tensors must stay alive while the plan
+    is used; the plan keeps references to them."""
+
+    def __init__(self, inputs, outputs, dtype="f64"):
+        import torch
+        code = _dtype_code(dtype)
+        td = _torch_dtype(code)
+        G = len(inputs)
+        if len(outputs) != G:
+            raise ValueError("inputs and outputs must list the same number of grids")
+        InTabs = (ctypes.c_void_p * (N_IN * max(G, 1)))()
+        OutTabs = (ctypes.c_void_p * (N_OUT * max(G, 1)))()
+        ns = (ctypes.c_int64 * max(G, 1))()
+        dev = None
+        for d in range(G):
+            rows = _rows(inputs[d], N_IN, "inputs[%d]" % d)
+            orows = _rows(outputs[d], N_OUT, "outputs[%d]" % d)
+            n = rows[0].shape[0]
+            dev = dev or rows[0].device
+            it = _table(rows, N_IN, n, td, "cuda", "inputs[%d]" % d)
+            ot = _table(orows, N_OUT, n, td, "cuda", "outputs[%d]" % d)
+            if n == 0:
+                _nonnull_empty(it, N_IN)
+                _nonnull_empty(ot, N_OUT)
+            for s in range(N_IN):
+                InTabs[d * N_IN + s] = it[s]
+            for s in range(N_OUT):
+                OutTabs[d * N_OUT + s] = ot[s]
+            ns[d] = n
+        self.device = dev if dev is not None else torch.device("cuda", torch.cuda.current_device())
+        self._keep = (list(inputs), list(outputs))
+        self.G = G
+        self.dtype = dtype
+        h = ctypes.c_void_p()
+        L = _batch_lib()
+        with torch.cuda.device(self.device):
+            _check(L.tl_dtg_batched_prepare(ctypes.byref(InTabs), ctypes.byref(OutTabs), ctypes.byref(ns), G, code,
+                                            ctypes.byref(h)))
+        self._h = h
+
+    def launch(self, stream=None):
+        import torch
+        with torch.cuda.device(self.device):
+            _check(_batch_lib().tl_dtg_batched(self._h, _stream_handle(stream, self.device)))
+
+    def tune(self, stream=None):
+        import torch
+        with torch.cuda.device(self.device):
+            _check(_batch_lib().tl_dtg_batched_tune(self._h, _stream_handle(stream, self.device)))
+        return self.config
+
+    @property
+    def config(self):
+        t, b = ctypes.c_int32(), ctypes.c_int32()
+        _check(_batch_lib().tl_batch_plan_config(self._h, ctypes.byref(t), ctypes.byref(b)))
+        return t.value, b.value
+
+    def set_config(self, threads, blocks_per_sm):
+        _check(_batch_lib().tl_batch_plan_set_config(self._h, threads, blocks_per_sm))
+
+    def check(self):
+        import torch
+        with torch.cuda.device(self.device):
+            _check(_batch_lib().tl_batch_plan_check(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _batch_lib().tl_batch_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def tl_dtg_batched_prepare(inputs, outputs, dtype="f64"):
+    """inputs: list of G [43, n_d] device tensors; outputs: list of G [39, n_d].  Returns a BatchPlan."""
+    return BatchPlan(inputs, outputs, dtype)
+
+
+def tl_dtg_batched(plan, stream=None):
+    plan.launch(stream)
+
+
+def tl_dtg_batched_tune(plan, stream=None):
+    return plan.tune(stream)

@@ -7,6 +7,7 @@
 // kernels (one thread per point and output component, one kernel per expression, pointer tables
 // read from global memory; Sec. 4), the whole chain is one kernel and the pointer tables are kernel
 // parameters.
+#include "dtg_batched.cuh"
 #include "dtg_fwd_body.cuh"
 
 namespace tl {
@@ -112,6 +113,60 @@ __global__ void __launch_bounds__(kFwdThreads) dtg_fwd_f32_kernel(const FwdArgs<
     for (int64_t x = gs.first; x < n; x += gs.step)
         if (!fwd_point_f32<true>(a, x))
             fwd_point_f32_general(a, x);
+}
+
+// ------------------------------------------------------------------------------------ batched forward
+template <int kThreads>
+__global__ void __launch_bounds__(kThreads) dtg_batched_f64_kernel(const BatchView v)
+{
+    __shared__ FwdArgs<double> s_args;
+    batched_loop<double>(v, s_args, [](const FwdArgs<double> &a, int64_t x) { fwd_point_f64(a, x); });
+}
+
+template <int kThreads>
+__global__ void __launch_bounds__(kThreads) dtg_batched_f32_kernel(const BatchView v)
+{
+    __shared__ FwdArgs<float> s_args;
+    batched_loop<float>(v, s_args, [](const FwdArgs<float> &a, int64_t x) {
+        if (!fwd_point_f32<true>(a, x))
+            fwd_point_f32_general(a, x);
+    });
+}
+
+template <typename K> static cudaError_t launch_k(K k, const BatchView &v, int threads, int grid, cudaStream_t s)
+{
+    k<<<grid, threads, 0, s>>>(v);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batched(int dtype, const BatchView &v, int threads, int grid, cudaStream_t s)
+{
+    if (dtype == 2)
+        return launch_batched_ff(v, threads, grid, s);
+    switch (threads) {
+    case 128: return dtype == 0 ? launch_k(dtg_batched_f64_kernel<128>, v, 128, grid, s)
+                                : launch_k(dtg_batched_f32_kernel<128>, v, 128, grid, s);
+    case 256: return dtype == 0 ? launch_k(dtg_batched_f64_kernel<256>, v, 256, grid, s)
+                                : launch_k(dtg_batched_f32_kernel<256>, v, 256, grid, s);
+    case 512: return dtype == 0 ? launch_k(dtg_batched_f64_kernel<512>, v, 512, grid, s)
+                                : launch_k(dtg_batched_f32_kernel<512>, v, 512, grid, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t occupancy_batched(int dtype, int threads, int *blocks)
+{
+    if (dtype == 2)
+        return occupancy_batched_ff(threads, blocks);
+    switch (threads) {
+    case 128: return dtype == 0 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, dtg_batched_f64_kernel<128>, 128, 0)
+                                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, dtg_batched_f32_kernel<128>, 128, 0);
+    case 256: return dtype == 0 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, dtg_batched_f64_kernel<256>, 256, 0)
+                                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, dtg_batched_f32_kernel<256>, 256, 0);
+    case 512: return dtype == 0 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, dtg_batched_f64_kernel<512>, 512, 0)
+                                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, dtg_batched_f32_kernel<512>, 512, 0);
+    }
+    return cudaErrorInvalidValue;
 }
 
 // ------------------------------------------------------------------------------------------- launchers

@@ -9,6 +9,7 @@
 // integer operations (ff.cuh).  FP64 work drops to ~45 operations per point.  Points whose values
 // fall outside the pair format's safe range (|x| >= 2^63, inf, nan) are evaluated by the
 // all-binary64 path instead.
+#include "dtg_batched.cuh"
 #include "dtg_fwd_body.cuh"
 #include <algorithm>
 
@@ -123,6 +124,34 @@ cudaError_t launch_fwd_ff(const FwdArgs<double> &a, int64_t n, int grid, cudaStr
 {
     dtg_fwd_ff_kernel<<<grid, kFwdThreads, 0, s>>>(a, n);
     return cudaGetLastError();
+}
+
+template <int kThreads>
+__global__ void __launch_bounds__(kThreads) dtg_batched_ff_kernel(const BatchView v)
+{
+    __shared__ FwdArgs<double> s_args;
+    batched_loop<double>(v, s_args, [](const FwdArgs<double> &a, int64_t x) { fwd_point_ff(a, x); });
+}
+
+cudaError_t launch_batched_ff(const BatchView &v, int threads, int grid, cudaStream_t s)
+{
+    switch (threads) {
+    case 128: dtg_batched_ff_kernel<128><<<grid, 128, 0, s>>>(v); break;
+    case 256: dtg_batched_ff_kernel<256><<<grid, 256, 0, s>>>(v); break;
+    case 512: dtg_batched_ff_kernel<512><<<grid, 512, 0, s>>>(v); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t occupancy_batched_ff(int threads, int *blocks)
+{
+    switch (threads) {
+    case 128: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, dtg_batched_ff_kernel<128>, 128, 0);
+    case 256: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, dtg_batched_ff_kernel<256>, 256, 0);
+    case 512: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, dtg_batched_ff_kernel<512>, 512, 0);
+    }
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t occupancy_fwd_ff(int *ff_blocks)

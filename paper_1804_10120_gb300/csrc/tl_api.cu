@@ -8,10 +8,10 @@
 #include <vector>
 
 #include "../../include/tl.h"
+#include "tl_host.h"
 #include "tl_kernels.h"
 
 namespace tl {
-namespace {
 
 thread_local std::string g_last_error;
 
@@ -32,13 +32,6 @@ tl_status cuda_fail(cudaError_t e, const char *what)
 }
 
 // ---- per-device facts, queried once ------------------------------------------------------------------
-constexpr int kMaxDevices = 64;
-struct DeviceInfo {
-    bool ready = false;
-    bool supported = false;
-    int sms = 0;
-    int fwd_f64_blocks = 0, fwd_f32_blocks = 0, fwd_ff_blocks = 0, bwd_f64_blocks = 0, bwd_ff_blocks = 0;
-};
 DeviceInfo g_dev[kMaxDevices];
 std::mutex g_dev_mu;
 
@@ -59,6 +52,13 @@ tl_status device_info(const DeviceInfo **out)
             (e = cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
             return cuda_fail(e, "cudaDeviceGetAttribute");
         d.supported = (major == 10 && minor == 3);
+        cudaDeviceProp prop;
+        if (cudaGetDeviceProperties(&prop, dev) == cudaSuccess) {
+            strncpy(d.name, prop.name, sizeof d.name - 1);
+            for (char *c = d.name; *c; ++c)
+                if (*c == ' ' || *c == '|')
+                    *c = '_';
+        }
         if (d.supported) {
             e = occupancy_fwd(&d.fwd_f64_blocks, &d.fwd_f32_blocks, &d.fwd_ff_blocks);
             if (e == cudaSuccess)
@@ -85,37 +85,58 @@ int grid_for(int64_t n, int threads, int sms, int blocks_per_sm)
 size_t elem_size(tl_dtype t) { return t == TL_F32 ? 4 : 8; }
 bool dtype_ok(int t) { return t == TL_F64 || t == TL_F32 || t == TL_F64_FF; }
 
-struct Range {
-    uintptr_t lo, hi;
-    int table, index;
-};
-
-// All pointers non-null and element-aligned; no written range overlaps any other range.
-tl_status check_tables(const void *const *tabs[], const int counts[], const bool writes[], const bool nullable[],
-                       const char *const names[], int ntabs, int64_t n, size_t esz)
+// Collect the ranges of a set of tables: all pointers non-null (unless nullable) and element-aligned.
+tl_status collect_ranges(std::vector<Range> &rs, const void *const *tabs[], const int counts[], const bool writes[],
+                         const bool nullable[], const char *const names[], int ntabs, int64_t n, size_t esz, int grid)
 {
-    std::vector<Range> rs;
-    rs.reserve(128);
     for (int t = 0; t < ntabs; ++t)
         for (int s = 0; s < counts[t]; ++s) {
             const void *p = tabs[t][s];
             if (!p) {
                 if (nullable[t])
                     continue;
-                return fail(TL_ERR_INVALID_ARG, "%s[%d] is NULL", names[t], s);
+                return grid < 0 ? fail(TL_ERR_INVALID_ARG, "%s[%d] is NULL", names[t], s)
+                                : fail(TL_ERR_INVALID_ARG, "grid %d: %s[%d] is NULL", grid, names[t], s);
             }
             if ((uintptr_t)p % esz)
                 return fail(TL_ERR_ALIGNMENT, "%s[%d]=%p is not %zu-byte aligned", names[t], s, p, esz);
-            rs.push_back({(uintptr_t)p, (uintptr_t)p + (uintptr_t)n * esz, t, s});
+            if (n > 0)
+                rs.push_back({(uintptr_t)p, (uintptr_t)p + (uintptr_t)n * esz, writes[t], names[t], s, grid});
         }
-    std::sort(rs.begin(), rs.end(), [](const Range &a, const Range &b) { return a.lo < b.lo; });
-    // sweep: any written range that intersects a neighbour is an error (read/read overlap is allowed)
-    for (size_t i = 0; i < rs.size(); ++i)
-        for (size_t j = i + 1; j < rs.size() && rs[j].lo < rs[i].hi; ++j)
-            if (writes[rs[i].table] || writes[rs[j].table])
-                return fail(TL_ERR_INVALID_ARG, "%s[%d] overlaps %s[%d] (outputs must not alias)",
-                            names[rs[i].table], rs[i].index, names[rs[j].table], rs[j].index);
     return TL_OK;
+}
+
+// No written range may intersect any other range (read/read overlap is allowed).
+tl_status check_overlaps(std::vector<Range> &rs)
+{
+    std::sort(rs.begin(), rs.end(), [](const Range &a, const Range &b) { return a.lo < b.lo; });
+    // sweep with the furthest-reaching written and any range seen so far
+    size_t open_any = SIZE_MAX, open_w = SIZE_MAX;
+    for (size_t i = 0; i < rs.size(); ++i) {
+        const Range &r = rs[i];
+        const Range *hit = nullptr;
+        if (r.write && open_any != SIZE_MAX && rs[open_any].hi > r.lo)
+            hit = &rs[open_any];
+        else if (open_w != SIZE_MAX && rs[open_w].hi > r.lo)
+            hit = &rs[open_w];
+        if (hit)
+            return fail(TL_ERR_INVALID_ARG, "%s[%d] (grid %d) overlaps %s[%d] (grid %d): outputs must not alias",
+                        hit->name, hit->index, hit->grid, r.name, r.index, r.grid);
+        if (open_any == SIZE_MAX || r.hi > rs[open_any].hi)
+            open_any = i;
+        if (r.write && (open_w == SIZE_MAX || r.hi > rs[open_w].hi))
+            open_w = i;
+    }
+    return TL_OK;
+}
+
+tl_status check_tables(const void *const *tabs[], const int counts[], const bool writes[], const bool nullable[],
+                       const char *const names[], int ntabs, int64_t n, size_t esz)
+{
+    std::vector<Range> rs;
+    rs.reserve(128);
+    tl_status s = collect_ranges(rs, tabs, counts, writes, nullable, names, ntabs, n, esz, -1);
+    return s != TL_OK ? s : check_overlaps(rs);
 }
 
 template <typename T> FwdArgs<T> fwd_args(const tl_dtg_in *in, const tl_dtg_out *out)
@@ -210,7 +231,6 @@ tl_status host_lanes(HostLanes **out)
     return TL_OK;
 }
 
-}  // namespace
 }  // namespace tl
 
 using namespace tl;

@@ -16,6 +16,14 @@ cudaError_t launch_fwd_ff(const FwdArgs<double> &a, int64_t n, int grid, cudaStr
 cudaError_t launch_bwd_f64(const BwdArgs<double> &a, int64_t n, int grid, cudaStream_t s);
 cudaError_t launch_bwd_ff(const BwdArgs<double> &a, int64_t n, int grid, cudaStream_t s);
 
+struct BatchView;
+// Batched forward: one persistent launch over all grids of a plan; `threads` in {128, 256, 512}.
+cudaError_t launch_batched(int dtype, const BatchView &v, int threads, int grid, cudaStream_t s);
+// Resident blocks per SM of the batched kernel for dtype and block size.
+cudaError_t occupancy_batched(int dtype, int threads, int *blocks);
+cudaError_t launch_batched_ff(const BatchView &v, int threads, int grid, cudaStream_t s);
+cudaError_t occupancy_batched_ff(int threads, int *blocks);
+
 // Resident blocks per SM of each kernel (0 where a kernel is not provided).
 cudaError_t occupancy_fwd(int *f64, int *f32, int *ff);
 cudaError_t occupancy_bwd(int *f64, int *ff);

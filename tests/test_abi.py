@@ -90,3 +90,25 @@ def test_host_workspace_size(L):
     assert L.tl_dtg_host_workspace_bytes(100, 1) == 100 * 82 * 4
     big = 1 << 24
     assert L.tl_dtg_host_workspace_bytes(big, 0) == 2 * (1 << 20) * 82 * 8
+
+
+def test_batched_prepare_argument_checks(L):
+    """Batch validation runs on the host before any device work: overlaps across grids, NULL entries
+    and negative sizes are rejected."""
+    vp = ctypes.c_void_p
+    L.tl_dtg_batched_prepare.argtypes = [vp, vp, vp, ctypes.c_int32, ctypes.c_int, ctypes.POINTER(vp)]
+    L.tl_dtg_batched_prepare.restype = ctypes.c_int
+    G, n = 3, 16
+    ins = (vp * (43 * G))(*[(1 << 24) + (d * 82 + s) * n * 8 for d in range(G) for s in range(43)])
+    outs = (vp * (39 * G))(*[(1 << 24) + (d * 82 + 43 + s) * n * 8 for d in range(G) for s in range(39)])
+    ns = (ctypes.c_int64 * G)(n, n, n)
+    h = vp()
+    bad = (vp * (39 * G))(*outs); bad[39 + 5] = ins[0]            # grid 1 writes over grid 0's g_00
+    assert L.tl_dtg_batched_prepare(ctypes.byref(ins), ctypes.byref(bad), ctypes.byref(ns), G, 0, ctypes.byref(h)) == 1
+    assert b"overlap" in L.tl_last_error()
+    nul = (vp * (43 * G))(*ins); nul[43 * 2 + 7] = None
+    assert L.tl_dtg_batched_prepare(ctypes.byref(nul), ctypes.byref(outs), ctypes.byref(ns), G, 0, ctypes.byref(h)) == 1
+    neg = (ctypes.c_int64 * G)(n, -1, n)
+    assert L.tl_dtg_batched_prepare(ctypes.byref(ins), ctypes.byref(outs), ctypes.byref(neg), G, 0, ctypes.byref(h)) == 1
+    assert L.tl_dtg_batched_prepare(ctypes.byref(ins), ctypes.byref(outs), ctypes.byref(ns), -1, 0, ctypes.byref(h)) == 1
+    assert L.tl_dtg_batched_prepare(ctypes.byref(ins), ctypes.byref(outs), ctypes.byref(ns), G, 9, ctypes.byref(h)) == 1

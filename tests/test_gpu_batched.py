@@ -1,0 +1,137 @@
+"""Batched multi-grid forward (one persistent launch over many uneven subgrids) against the oracle and
+bit for bit against the single-grid kernel, in and out of a CUDA graph, before and after tuning."""
+import numpy as np
+import pytest
+
+import gridgen
+import oracle
+from tests.parity import TOL_F64, assert_components
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def dev():
+    return torch.device("cuda", 0)
+
+
+def make_batch(sides, seed, dtype=torch.float64):
+    """One grid per side (n = side^3), grid d drawing from its own streams (base 64 d)."""
+    xs, ys, hosts = [], [], []
+    for d, side in enumerate(sides):
+        n = side ** 3
+        x = gridgen.random_grid(n, seed, stream_base=gridgen.STREAMS_PER_FIELD * d)
+        hosts.append(x)
+        xs.append(torch.from_numpy(x).to(dev(), dtype))
+        ys.append(torch.full((39, n), float("nan"), dtype=dtype, device=dev()))
+    return hosts, xs, ys
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f64_ff"])
+def test_small_batch_matches_oracle_and_single_grid(dtype):
+    import paper_1804_10120_gb300 as tl
+    sides = [8, 3, 12, 1, 9, 16, 5, 0, 10]
+    hosts, xs, ys = make_batch(sides, 21)
+    plan = tl.tl_dtg_batched_prepare(xs, ys, dtype=dtype)
+    plan.launch()
+    plan.check()
+    for x, xd, y in zip(hosts, xs, ys):
+        yb = y.cpu().numpy()
+        assert_components(yb, oracle.forward(x), TOL_F64, what="batched %s" % dtype)
+        ys_single = tl.tl_dtg_forward(xd, dtype=dtype)
+        torch.cuda.synchronize()
+        assert np.array_equal(ys_single.cpu().numpy(), yb)   # same per-point code: bitwise
+    plan.close()
+
+
+def test_every_config_and_graph_capture():
+    import paper_1804_10120_gb300 as tl
+    sides = [int(s) for s in np.random.default_rng(5).integers(2, 20, 40)]
+    hosts, xs, ys = make_batch(sides, 22)
+    plan = tl.BatchPlan(xs, ys)
+    refs = [tl.tl_dtg_forward(x) for x in xs]
+    torch.cuda.synchronize()
+    for threads in (128, 256, 512):
+        for bps in (1, 2):
+            for y in ys:
+                y.fill_(float("nan"))
+            try:
+                plan.set_config(threads, bps)
+            except tl.TLError as e:              # beyond this kernel's occupancy
+                assert e.status == 1
+                continue
+            plan.launch()
+            torch.cuda.synchronize()
+            for y, r in zip(ys, refs):
+                assert torch.equal(y, r), (threads, bps)
+    # CUDA graph: capture one launch, replay twice
+    for y in ys:
+        y.fill_(float("nan"))
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        plan.launch(stream=s)
+    g.replay()
+    g.replay()
+    torch.cuda.synchronize()
+    for y, r in zip(ys, refs):
+        assert torch.equal(y, r)
+    plan.check()
+
+
+def test_tuner_picks_a_valid_config(tmp_path, monkeypatch):
+    import paper_1804_10120_gb300 as tl
+    monkeypatch.setenv("TL_TUNE_CACHE", str(tmp_path / "tune.txt"))
+    sides = [16, 20, 24, 12]
+    hosts, xs, ys = make_batch(sides, 23)
+    plan = tl.BatchPlan(xs, ys)
+    t, b = plan.tune()
+    assert t in (128, 256, 512) and b >= 1
+    text = (tmp_path / "tune.txt").read_text()
+    assert "batched" in text and ("%d %d" % (t, b)) in text
+    plan2 = tl.BatchPlan(xs, ys)             # same shape: configuration from the cache
+    assert plan2.config == (t, b)
+    plan2.launch()
+    torch.cuda.synchronize()
+    for x, y in zip(hosts, ys):
+        assert_components(y.cpu().numpy(), oracle.forward(x), TOL_F64, what="tuned")
+
+
+def test_multi_domain_600_grids_sampled():
+    """600 subgrids, side ~ U{8..48} (seed 2): parity on a sample of grids, bitwise equality with the
+    single-grid kernel on every grid."""
+    import paper_1804_10120_gb300 as tl
+    sides = gridgen.subgrid_sides(600, 2)
+    assert min(sides) >= 8 and max(sides) <= 48
+    hosts, xs, ys = make_batch(sides, 2)
+    plan = tl.BatchPlan(xs, ys)
+    plan.launch()
+    torch.cuda.synchronize()
+    plan.check()
+    for d in range(0, 600, 37):
+        assert_components(ys[d].cpu().numpy(), oracle.forward(hosts[d]), TOL_F64, what="grid %d" % d)
+    for x, y in zip(xs, ys):
+        assert torch.equal(tl.tl_dtg_forward(x), y)
+
+
+def test_empty_batch():
+    import paper_1804_10120_gb300 as tl
+    plan = tl.BatchPlan([], [])
+    plan.launch()
+    plan.check()
+    x = torch.empty((43, 0), dtype=torch.float64, device=dev())
+    y = torch.empty((39, 0), dtype=torch.float64, device=dev())
+    plan = tl.BatchPlan([x], [y])
+    plan.launch()
+    plan.check()
+
+
+def test_f32_batch():
+    import paper_1804_10120_gb300 as tl
+    sides = [7, 13, 4]
+    hosts, xs, ys = make_batch(sides, 24, dtype=torch.float32)
+    plan = tl.BatchPlan(xs, ys, dtype="f32")
+    plan.launch()
+    for x, y in zip(xs, ys):
+        assert torch.equal(tl.tl_dtg_forward(x, dtype="f32"), y)
