@@ -140,6 +140,27 @@ TL_API tl_status tl_batch_plan_set_config(tl_batch_plan *plan, int32_t threads, 
 TL_API tl_status tl_batch_plan_check(const tl_batch_plan *plan);
 TL_API void tl_batch_plan_destroy(tl_batch_plan *plan);
 
+/*
+ * tl_dtg_batched_noalloc -- the batched forward for callers that cannot let a library allocate device
+ * memory: code whose device memory is owned by a caching allocator or a fixed budget, loops that cannot
+ * afford cudaMalloc's implicit device-wide synchronisation, or plug-ins handed only their buffers.  The
+ * paper has no counterpart (it is an interface choice of this library).
+ *
+ * Same grids, layout, dtype and validation as tl_dtg_batched_prepare + tl_dtg_batched, but no plan: the
+ * kernel's scratch (pointer tables, sizes, tile prefix sums, status word) lives in one fixed device
+ * array inside the library, 688,392 bytes, which every GPU that loads the library holds until exit.
+ * At most 1024 grids (G > 1024 returns TL_ERR_INVALID_ARG); 256 threads per block, no tuning.
+ * Nothing is allocated by the library -- no cudaMalloc / cudaFree, no allocating library routine.
+ * The first call on a device performs a one-time set-up on that device (it resolves the array's
+ * device address), so make that first call before any stream capture.  Each call copies the tables
+ * from host memory into the array on `stream` (these copies come from pageable memory and synchronise
+ * with the host), then launches.  Every call shares the one array and leaves its contents behind:
+ * calls whose work overlaps on the GPU (different streams, or host threads racing) corrupt each
+ * other's tables -- order them on one stream.  Error behaviour as for the other entry points.
+ */
+TL_API tl_status tl_dtg_batched_noalloc(const tl_dtg_in *in, const tl_dtg_out *out, const int64_t *n, int32_t G,
+                                        tl_dtype dtype, tl_stream stream);
+
 TL_API const char *tl_status_string(tl_status s);
 TL_API const char *tl_last_error(void);
 /* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
