@@ -34,14 +34,17 @@ KERNEL_NAME = {"f64": "dtg_fwd_f64_kernel", "f64_ff": "dtg_fwd_ff_kernel", "f32"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--variant", default=os.environ.get("TL_BENCH_VARIANT", "f64"), choices=["f64", "f64_ff", "f32"])
     ap.add_argument("--n", type=int, default=N_FULL)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--no-extras", action="store_true", help="skip the secondary variant measurements")
+    ap.add_argument("--no-extras", action="store_true", help="skip the measurements of the other forms")
+    ap.add_argument("--only", default=None, choices=["forward", "adjoint", "batched"],
+                    help="run just one form on --n points (or --grids subgrids) and print its timing; for profiling")
+    ap.add_argument("--grids", type=int, default=600)
     return ap.parse_args()
 
 
@@ -194,9 +197,9 @@ def reference_arm(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded random grid)",
-        "config": {"workload": "fused forward, single grid N=2^24 (256^3) FP64 SoA, seed 1; each reference step "
-                               "runs the CPU oracle on the first %d points" % n_sample,
-                   "global_batch": n_sample, "parallelism": "host threads"},
+        "config": {"workload": "fused forward chain, single grid N=2^24 (256^3), SoA, seed 1",
+                   "sample": "each reference step runs the CPU oracle on the first %d points of that grid" % n_sample,
+                   "global_batch": n_sample, "parallelism": "host threads (%d)" % threads},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": "%d points per step (first points of the N=2^24 seed-1 grid)" % n_sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -205,10 +208,150 @@ def reference_arm(args):
     print(json.dumps(line), flush=True)
 
 
+# Algorithmic work per grid point (the design doc derives both):
+#   bytes: 8 x (43 + 39) for binary64, 4 x 82 for binary32 (each component array crosses HBM once);
+#   binary64 flops of the fused chain as this library formulates it (FMA = 2): inverse 35, Eq. 3 bracket
+#   18, Eq. 3 contraction 90, covariant shift derivative 54, Eq. 2 15.
+FLOPS_F64_PER_POINT = 212
+FP64_TFLOPS_PEAK = 2 * 2 * 152 * 2.07e9 / 1e12   # 2 DFMA / clk / SM x 2 flop x 152 SMs x 2070 MHz
+
+
+def cuda_time(fn, steps, stream, warmup=3):
+    """Mean ms per call of fn over `steps` calls, CUDA events on `stream`, after `warmup` calls."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def extras(dev, stream, steps, x64, hbm):
+    """The other forms of the path, each against the plain binary64 single-grid kernel, same GPU."""
+    import torch
+    import gridgen
+    import paper_1804_10120_gb300 as tl
+    out = {}
+    n = x64.shape[1]
+    y = torch.empty((39, n), dtype=torch.float64, device=dev)
+    ms = cuda_time(lambda: tl.tl_dtg_forward(x64, y, dtype="f64_ff", stream=stream), steps, stream)
+    out["f64_ff_forward"] = {"workload": "single grid N=2^24, seed 1", "ms": ms, "points_per_s": n / ms * 1e3,
+                             "GB_s": 656 * n / ms / 1e6, "hbm_frac": 656 * n / ms / 1e6 / hbm,
+                             "arith": "binary64 inverse, Eq. 3 bracket and Eq. 2; float-float contractions"}
+    del y
+    x32 = x64.float()
+    y32 = torch.empty((39, n), dtype=torch.float32, device=dev)
+    ms = cuda_time(lambda: tl.tl_dtg_forward(x32, y32, dtype="f32", stream=stream), steps, stream)
+    out["f32_forward"] = {"workload": "single grid N=2^24, seed 1 rounded to binary32", "ms": ms,
+                          "points_per_s": n / ms * 1e3, "GB_s": 328 * n / ms / 1e6, "hbm_frac": 328 * n / ms / 1e6 / hbm,
+                          "arith": "binary32; det(g) and inverse in binary64"}
+    del x32, y32
+    # forward + adjoint, N = 2^22, loss sum W dtg + V Gamma (seed 3)
+    n3 = 1 << 22
+    x3 = torch.from_numpy(gridgen.random_grid(n3, 3)).to(dev)
+    W = torch.from_numpy(gridgen.normal_fields(6, n3, 3, 1000)).to(dev)
+    V = torch.from_numpy(gridgen.normal_fields(18, n3, 3, 1100)).to(dev)
+    gout = [None] * 6 + [V[i] for i in range(18)] + [None] * 9 + [W[i] for i in range(6)]
+    y3 = torch.empty((39, n3), dtype=torch.float64, device=dev)
+    g3 = torch.empty((43, n3), dtype=torch.float64, device=dev)
+    ms_f = cuda_time(lambda: tl.tl_dtg_forward(x3, y3, stream=stream), steps, stream)
+    ms_b = cuda_time(lambda: tl.tl_dtg_backward(x3, gout, g3, stream=stream), steps, stream)
+    ms_fb = cuda_time(lambda: (tl.tl_dtg_forward(x3, y3, stream=stream), tl.tl_dtg_backward(x3, gout, g3, stream=stream)),
+                      steps, stream)
+    out["fwd_adjoint"] = {"workload": "N=2^22, seed 3, L = sum W dtg + V Gamma", "ms_forward": ms_f,
+                          "ms_adjoint": ms_b, "ms": ms_fb, "points_per_s": n3 / ms_fb * 1e3,
+                          "GB_s": 1536 * n3 / ms_fb / 1e6, "hbm_frac": 1536 * n3 / ms_fb / 1e6 / hbm,
+                          "adjoint_GB_s": 880 * n3 / ms_b / 1e6}
+    del x3, W, V, gout, y3, g3
+    # batched: 600 subgrids n^3, n ~ U{8..48} (seed 2)
+    sides = gridgen.subgrid_sides(600, 2)
+    xs, ys = [], []
+    for d, side in enumerate(sides):
+        nd = side ** 3
+        xs.append(torch.from_numpy(gridgen.random_grid(nd, 2, stream_base=gridgen.STREAMS_PER_FIELD * d)).to(dev))
+        ys.append(torch.empty((39, nd), dtype=torch.float64, device=dev))
+    tot = sum(side ** 3 for side in sides)
+    plan = tl.BatchPlan(xs, ys)
+    cfg = plan.tune(stream)
+    ms_b = cuda_time(lambda: plan.launch(stream), steps, stream)
+    g = torch.cuda.CUDAGraph()
+    side_stream = torch.cuda.Stream(dev)
+    side_stream.wait_stream(stream)
+    with torch.cuda.graph(g, stream=side_stream):
+        plan.launch(side_stream)
+    ms_bg = cuda_time(g.replay, steps, torch.cuda.current_stream(dev))
+
+    def separate():
+        for xd, yd in zip(xs, ys):
+            tl.tl_dtg_forward(xd, yd, stream=stream)
+    ms_sep = cuda_time(separate, max(2, steps // 10), stream)
+    g2 = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g2, stream=side_stream):
+        for xd, yd in zip(xs, ys):
+            tl.tl_dtg_forward(xd, yd, stream=side_stream)
+    ms_sepg = cuda_time(g2.replay, max(2, steps // 2), torch.cuda.current_stream(dev))
+    out["batched"] = {"workload": "600 subgrids, N_d = n^3, n ~ U{8..48} (seed 2), %d points" % tot,
+                      "config": {"threads": cfg[0], "blocks_per_sm": cfg[1]},
+                      "ms": ms_b, "points_per_s": tot / ms_b * 1e3, "GB_s": 656 * tot / ms_b / 1e6,
+                      "hbm_frac": 656 * tot / ms_b / 1e6 / hbm,
+                      "ms_in_graph": ms_bg,
+                      "ms_600_launches": ms_sep, "ms_600_launches_in_graph": ms_sepg}
+    plan.close()
+    del xs, ys
+    return out
+
+
+def only_form(args):
+    """One form alone, for profilers: forward (--variant), adjoint (binary64, loss W dtg + V Gamma) or
+    batched (--grids subgrids of the multi-domain recipe)."""
+    import torch
+    import gridgen
+    import paper_1804_10120_gb300 as tl
+    from paper_1804_10120_gb300 import build as tlbuild
+    tlbuild.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    n = args.n
+    if args.only == "forward":
+        td = torch.float32 if args.variant == "f32" else torch.float64
+        x = torch.from_numpy(gridgen.random_grid(n, 1)).to(dev, td)
+        y = torch.empty((39, n), dtype=td, device=dev)
+        fn = lambda: tl.tl_dtg_forward(x, y, dtype=args.variant, stream=stream)
+        units = n
+    elif args.only == "adjoint":
+        x = torch.from_numpy(gridgen.random_grid(n, 3)).to(dev)
+        W = torch.from_numpy(gridgen.normal_fields(6, n, 3, 1000)).to(dev)
+        V = torch.from_numpy(gridgen.normal_fields(18, n, 3, 1100)).to(dev)
+        gout = [None] * 6 + [V[i] for i in range(18)] + [None] * 9 + [W[i] for i in range(6)]
+        g = torch.empty((43, n), dtype=torch.float64, device=dev)
+        fn = lambda: tl.tl_dtg_backward(x, gout, g, stream=stream)
+        units = n
+    else:
+        sides = gridgen.subgrid_sides(args.grids, 2)
+        xs, ys = [], []
+        for d, side in enumerate(sides):
+            xs.append(torch.from_numpy(gridgen.random_grid(side ** 3, 2, stream_base=gridgen.STREAMS_PER_FIELD * d)).to(dev))
+            ys.append(torch.empty((39, side ** 3), dtype=torch.float64, device=dev))
+        plan = tl.BatchPlan(xs, ys, dtype=args.variant if args.variant != "f32" else "f64")
+        fn = lambda: plan.launch(stream)
+        units = sum(side ** 3 for side in sides)
+    ms = cuda_time(fn, args.steps, stream, warmup=args.warmup)
+    print(json.dumps({"form": args.only, "variant": args.variant, "points": units, "ms": ms,
+                      "points_per_s": units / ms * 1e3}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.only:
+        return only_form(args)
     import numpy as np
     import torch
     import torch.distributed as dist
@@ -265,8 +408,22 @@ def main():
     avg_launch_s = statistics.mean(per) * 1e-3
     hbm, peak_kind = peaks()
     bpp = BYTES_PER_POINT[variant]
-    achieved = bpp * n / avg_launch_s / 1e9
+    gbs = bpp * n / avg_launch_s / 1e9
     traffic = traffic_per_launch(KERNEL_NAME[variant], n)
+    if variant == "f64":
+        # binary64 arithmetic is bound by the FP64 pipe (1/64 of the FP32 rate on this part), not by HBM
+        tf = FLOPS_F64_PER_POINT * n / avg_launch_s / 1e12
+        roofline = {"bound": "alu", "achieved": tf, "peak": FP64_TFLOPS_PEAK, "unit": "TFLOP/s",
+                    "frac": tf / FP64_TFLOPS_PEAK, "traffic": traffic,
+                    "peak_source": "FP64 pipe: 2 DFMA/clk/SM x 152 SMs x 2070 MHz (1.26 TFLOP/s; cf. nominal 1.25)",
+                    "kernel": KERNEL_NAME[variant], "flops_per_point": FLOPS_F64_PER_POINT,
+                    "avg_launch_ms": avg_launch_s * 1e3,
+                    "hbm": {"achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                            "bytes_per_point": bpp, "peak_source": peak_kind}}
+    else:
+        roofline = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                    "traffic": traffic, "peak_source": peak_kind, "kernel": KERNEL_NAME[variant],
+                    "bytes_per_point": bpp, "avg_launch_ms": avg_launch_s * 1e3}
 
     # end to end through the host-buffer C entry point: H2D of the inputs and D2H of the outputs inside
     # the timed region, page-locked host memory
@@ -295,6 +452,10 @@ def main():
                "steps": e2e_steps, "entry_point": "tl_dtg_forward_host"}
         del ws, y_pinned
 
+    forms = None
+    if rank == 0 and world == 1 and not args.no_extras and variant != "f32" and n == N_FULL:
+        forms = extras(dev, stream, max(5, min(args.steps, 20)), x, hbm)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         v, cores, sample = time_oracle(x_host)
@@ -305,20 +466,18 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": {"f64": "f64", "f64_ff": "f64", "f32": "f32"}[variant],
+            "dtype": {"f64": "f64", "f64_ff": "f64 storage, float-float contractions", "f32": "f32"}[variant],
             "data": "synthetic (seeded random grid: g = delta + 0.1 S, dg ~ U[-0.1,0.1], K, beta, dbeta ~ N(0,0.1), alpha ~ U[0.5,1.5])",
             "config": {"workload": "fused forward chain, single grid N=2^24 (256^3), SoA, seed 1",
                        "variant": variant, "global_batch": world * n, "points_per_gpu": n,
                        "parallelism": "replicas (independent grids per GPU)" if world > 1 else "single GPU",
                        "l2": "inputs+outputs %.1f GB > 129 MB L2; no flush" % (82 * n * esz / 1e9)},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm, "traffic": traffic, "peak_source": peak_kind,
-                         "kernel": KERNEL_NAME[variant], "bytes_per_point": bpp,
-                         "avg_launch_ms": avg_launch_s * 1e3},
+            "roofline": roofline,
             "gpu_launches": args.steps,
             "clocks": clk.summary(),
             "e2e": e2e,
             "cpu_baseline": cpu,
+            "forms": forms,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

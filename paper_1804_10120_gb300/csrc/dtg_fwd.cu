@@ -38,17 +38,17 @@ __device__ __forceinline__ float narrow(double d, uint32_t &rare)
 template <bool kIntConv>
 __device__ __forceinline__ bool fwd_point_f32(const FwdArgs<float> &a, int64_t x)
 {
-    uint32_t rare = 0;
-    const double g00 = widen<kIntConv>(ld_stream(a.in[IN_G + 0] + x), rare),
-                 g01 = widen<kIntConv>(ld_stream(a.in[IN_G + 1] + x), rare),
-                 g02 = widen<kIntConv>(ld_stream(a.in[IN_G + 2] + x), rare),
-                 g11 = widen<kIntConv>(ld_stream(a.in[IN_G + 3] + x), rare),
-                 g12 = widen<kIntConv>(ld_stream(a.in[IN_G + 4] + x), rare),
-                 g22 = widen<kIntConv>(ld_stream(a.in[IN_G + 5] + x), rare);
-    float dg[18];
+    float v[N_IN];
 #pragma unroll
-    for (int s = 0; s < 18; ++s)
-        dg[s] = ld_stream(a.in[IN_DG + s] + x);
+    for (int s = 0; s < N_IN; ++s)
+        v[s] = ld_stream(a.in[s] + x);
+    asm volatile("" ::: "memory");   // every load is issued before any arithmetic
+
+    // step 1 in binary64 from the exactly widened metric; g^ij rounded once to binary32
+    uint32_t rare = 0;
+    const double g00 = widen<kIntConv>(v[IN_G + 0], rare), g01 = widen<kIntConv>(v[IN_G + 1], rare),
+                 g02 = widen<kIntConv>(v[IN_G + 2], rare), g11 = widen<kIntConv>(v[IN_G + 3], rare),
+                 g12 = widen<kIntConv>(v[IN_G + 4], rare), g22 = widen<kIntConv>(v[IN_G + 5], rare);
     double c[6];
     c[0] = fma(g11, g22, -(g12 * g12));
     c[1] = fma(g02, g12, -(g01 * g22));
@@ -69,6 +69,12 @@ __device__ __forceinline__ bool fwd_point_f32(const FwdArgs<float> &a, int64_t x
 #pragma unroll
     for (int p = 0; p < 6; ++p)
         st_stream(a.out[OUT_GINV + p] + x, gi[p]);
+
+    // step 2: Eq. 3
+    float dg[18];
+#pragma unroll
+    for (int s = 0; s < 18; ++s)
+        dg[s] = v[IN_DG + s];
     float T[3][6];
     christoffel_bracket<float>(dg, T);
     float gam[3][6];
@@ -79,27 +85,28 @@ __device__ __forceinline__ bool fwd_point_f32(const FwdArgs<float> &a, int64_t x
             gam[i][p] = fmaf(h[sym(i, 2)], T[2][p], fmaf(h[sym(i, 1)], T[1][p], h[sym(i, 0)] * T[0][p]));
             st_stream(a.out[OUT_GAMMA + 6 * i + p] + x, gam[i][p]);
         }
-    const float b0 = ld_stream(a.in[IN_BETA + 0] + x), b1 = ld_stream(a.in[IN_BETA + 1] + x),
-                b2 = ld_stream(a.in[IN_BETA + 2] + x);
+
+    // step 3: nabla_j beta_i = d_j beta_i - Gamma^k_ij beta_k
+    const float b0 = v[IN_BETA + 0], b1 = v[IN_BETA + 1], b2 = v[IN_BETA + 2];
     float nb[3][3];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
             const int p = sym(i, j);
-            const float B = ld_stream(a.in[IN_DBETA + 3 * i + j] + x);
-            nb[i][j] = fmaf(-gam[2][p], b2, fmaf(-gam[1][p], b1, fmaf(-gam[0][p], b0, B)));
+            nb[i][j] = fmaf(-gam[2][p], b2, fmaf(-gam[1][p], b1, fmaf(-gam[0][p], b0, v[IN_DBETA + 3 * i + j])));
             st_stream(a.out[OUT_DBCOV + 3 * i + j] + x, nb[i][j]);
         }
-    const float m2a = -2.0f * ld_stream(a.in[IN_ALPHA] + x);
+
+    // step 4: Eq. 2
+    const float m2a = -2.0f * v[IN_ALPHA];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
         for (int j = i; j < 3; ++j) {
             const int p = sym(i, j);
-            const float K = ld_stream(a.in[IN_K + p] + x);
             const float s = (i == j) ? 2.0f * nb[i][i] : nb[i][j] + nb[j][i];
-            st_stream(a.out[OUT_DTG + p] + x, fmaf(m2a, K, s));
+            st_stream(a.out[OUT_DTG + p] + x, fmaf(m2a, v[IN_K + p], s));
         }
     return true;
 }

@@ -12,6 +12,9 @@ namespace tl {
 template <typename R>
 __device__ __forceinline__ R dgc(const R (&dg)[18], int i, int j, int k) { return dg[3 * sym(i, j) + k]; }
 
+__device__ __forceinline__ double negate(double x) { return neg_exact(x); }
+__device__ __forceinline__ float negate(float x) { return -x; }
+
 template <typename R>
 __device__ __forceinline__ void christoffel_bracket(const R (&dg)[18], R (&T)[3][6])
 {
@@ -28,7 +31,7 @@ __device__ __forceinline__ void christoffel_bracket(const R (&dg)[18], R (&T)[3]
                 else if (l == k)
                     T[l][p] = D(k, k, j);
                 else if (j == k)
-                    T[l][p] = fma((R)2, D(j, l, j), -D(j, j, l));
+                    T[l][p] = fma((R)2, D(j, l, j), negate(D(j, j, l)));
                 else
                     T[l][p] = (D(j, l, k) + D(l, k, j)) - D(j, k, l);
             }
@@ -38,14 +41,19 @@ __device__ __forceinline__ void christoffel_bracket(const R (&dg)[18], R (&T)[3]
 // ------------------------------------------------------------------------------------ binary64 forward
 __device__ __forceinline__ void fwd_point_f64(const FwdArgs<double> &a, int64_t x)
 {
+    double v[N_IN];
+#pragma unroll
+    for (int s = 0; s < N_IN; ++s)
+        v[s] = ld_stream(a.in[s] + x);
+    asm volatile("" ::: "memory");   // every load is issued before any arithmetic
     // step 1: inverse metric by cofactors; det by first-row expansion
-    const double g00 = ld_stream(a.in[IN_G + 0] + x), g01 = ld_stream(a.in[IN_G + 1] + x),
-                 g02 = ld_stream(a.in[IN_G + 2] + x), g11 = ld_stream(a.in[IN_G + 3] + x),
-                 g12 = ld_stream(a.in[IN_G + 4] + x), g22 = ld_stream(a.in[IN_G + 5] + x);
+    const double g00 = v[IN_G + 0], g01 = v[IN_G + 1],
+                 g02 = v[IN_G + 2], g11 = v[IN_G + 3],
+                 g12 = v[IN_G + 4], g22 = v[IN_G + 5];
     double dg[18];
 #pragma unroll
     for (int s = 0; s < 18; ++s)
-        dg[s] = ld_stream(a.in[IN_DG + s] + x);
+        dg[s] = v[IN_DG + s];
 
     double c[6];
     c[0] = fma(g11, g22, -(g12 * g12));
@@ -77,27 +85,27 @@ __device__ __forceinline__ void fwd_point_f64(const FwdArgs<double> &a, int64_t 
         }
 
     // step 3: nabla_j beta_i = d_j beta_i - Gamma^k_ij beta_k
-    const double b0 = ld_stream(a.in[IN_BETA + 0] + x), b1 = ld_stream(a.in[IN_BETA + 1] + x),
-                 b2 = ld_stream(a.in[IN_BETA + 2] + x);
+    const double b0 = v[IN_BETA + 0], b1 = v[IN_BETA + 1],
+                 b2 = v[IN_BETA + 2];
     double nb[3][3];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
             const int p = sym(i, j);
-            const double B = ld_stream(a.in[IN_DBETA + 3 * i + j] + x);
+            const double B = v[IN_DBETA + 3 * i + j];
             nb[i][j] = fma(-gam[2][p], b2, fma(-gam[1][p], b1, fma(-gam[0][p], b0, B)));
             st_stream(a.out[OUT_DBCOV + 3 * i + j] + x, nb[i][j]);
         }
 
     // step 4: Eq. 2, d_t g_ij = -2 alpha K_ij + nabla_i beta_j + nabla_j beta_i
-    const double m2a = -twice_exact(ld_stream(a.in[IN_ALPHA] + x));
+    const double m2a = neg_exact(twice_exact(v[IN_ALPHA]));
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
         for (int j = i; j < 3; ++j) {
             const int p = sym(i, j);
-            const double K = ld_stream(a.in[IN_K + p] + x);
+            const double K = v[IN_K + p];
             const double s = (i == j) ? twice_exact(nb[i][i]) : nb[i][j] + nb[j][i];
             st_stream(a.out[OUT_DTG + p] + x, fma(m2a, K, s));
         }

@@ -6,7 +6,7 @@
 // determinant and inverse of g_ij, the bracket of Eq. 3 and Eq. 2 itself -- and evaluates the two
 // contractions, Gamma^i_jk = sum_l (g^il / 2) T_ljk (Eq. 3) and sum_k Gamma^k_ij beta_k (footnote to
 // Listing 1), in float-float pairs on the FP32 pipes, converting between binary64 and pairs with
-// integer operations (ff.cuh).  FP64 work drops to ~45 operations per point.  Points whose values
+// integer operations (ff.cuh).  FP64 work drops to ~54 operations per point.  Points whose values
 // fall outside the pair format's safe range (|x| >= 2^63, inf, nan) are evaluated by the
 // all-binary64 path instead.
 #include "dtg_batched.cuh"
@@ -19,15 +19,23 @@
 
 namespace tl {
 
+// The all-binary64 evaluation, out of line (only points outside the pair format's range take it).
+__device__ __noinline__ void fwd_point_f64_general(const FwdArgs<double> &a, int64_t x) { fwd_point_f64(a, x); }
+
 __device__ __forceinline__ void fwd_point_ff(const FwdArgs<double> &a, int64_t x)
 {
-    const double g00 = ld_stream(a.in[IN_G + 0] + x), g01 = ld_stream(a.in[IN_G + 1] + x),
-                 g02 = ld_stream(a.in[IN_G + 2] + x), g11 = ld_stream(a.in[IN_G + 3] + x),
-                 g12 = ld_stream(a.in[IN_G + 4] + x), g22 = ld_stream(a.in[IN_G + 5] + x);
+    double v[N_IN];
+#pragma unroll
+    for (int s = 0; s < N_IN; ++s)
+        v[s] = ld_stream(a.in[s] + x);
+    asm volatile("" ::: "memory");   // every load is issued before any arithmetic
+    const double g00 = v[IN_G + 0], g01 = v[IN_G + 1],
+                 g02 = v[IN_G + 2], g11 = v[IN_G + 3],
+                 g12 = v[IN_G + 4], g22 = v[IN_G + 5];
     double dg[18];
 #pragma unroll
     for (int s = 0; s < 18; ++s)
-        dg[s] = ld_stream(a.in[IN_DG + s] + x);
+        dg[s] = v[IN_DG + s];
 
     // step 1 in binary64
     double c[6];
@@ -58,18 +66,12 @@ __device__ __forceinline__ void fwd_point_ff(const FwdArgs<double> &a, int64_t x
         for (int p = 0; p < 6; ++p)
             T[l][p] = split_ff(Td[l][p], big);
 
-    const double b0 = ld_stream(a.in[IN_BETA + 0] + x), b1 = ld_stream(a.in[IN_BETA + 1] + x),
-                 b2 = ld_stream(a.in[IN_BETA + 2] + x);
-    double Bd[9];
-#pragma unroll
-    for (int q = 0; q < 9; ++q) {
-        Bd[q] = ld_stream(a.in[IN_DBETA + q] + x);
-        big |= out_of_ff_range(Bd[q]);   // split later, where it is used
-    }
+    const double b0 = v[IN_BETA + 0], b1 = v[IN_BETA + 1],
+                 b2 = v[IN_BETA + 2];
     const ff bf0 = split_ff(b0, big), bf1 = split_ff(b1, big), bf2 = split_ff(b2, big);
 
     if (big) {   // outside the pair format's range: the all-binary64 evaluation of this point
-        fwd_point_f64(a, x);
+        fwd_point_f64_general(a, x);
         return;
     }
 
@@ -83,31 +85,29 @@ __device__ __forceinline__ void fwd_point_ff(const FwdArgs<double> &a, int64_t x
             st_stream(a.out[OUT_GAMMA + 6 * i + p] + x, merge_ff(gam[i][p]));
         }
 
-    // step 3: S_ij = Gamma^k_ij beta_k (symmetric in ij: 6 sums) in pairs, nabla_j beta_i = d_j beta_i - S_ij
-    ff S6[6];
+    // step 3: S_ij = Gamma^k_ij beta_k (symmetric in ij: 6 sums) in pairs, then
+    // nabla_j beta_i = d_j beta_i - S_ij in binary64 (exactly d_j beta_i where S vanishes)
+    double S6[6];
 #pragma unroll
     for (int p = 0; p < 6; ++p)
-        S6[p] = dot3_ff(gam[0][p], bf0, gam[1][p], bf1, gam[2][p], bf2);
+        S6[p] = merge_ff(dot3_ff(gam[0][p], bf0, gam[1][p], bf1, gam[2][p], bf2));
     double nb[3][3];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
-            const ff &S = S6[sym(i, j)];
-            uint32_t unused = 0;
-            const ff B = split_ff(Bd[3 * i + j], unused);
-            nb[i][j] = merge_ff(sub_ff(B, S));
+            nb[i][j] = v[IN_DBETA + 3 * i + j] - S6[sym(i, j)];
             st_stream(a.out[OUT_DBCOV + 3 * i + j] + x, nb[i][j]);
         }
 
     // step 4: Eq. 2 in binary64
-    const double m2a = -twice_exact(ld_stream(a.in[IN_ALPHA] + x));
+    const double m2a = neg_exact(twice_exact(v[IN_ALPHA]));
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
         for (int j = i; j < 3; ++j) {
             const int p = sym(i, j);
-            const double K = ld_stream(a.in[IN_K + p] + x);
+            const double K = v[IN_K + p];
             const double s = (i == j) ? twice_exact(nb[i][i]) : nb[i][j] + nb[j][i];
             st_stream(a.out[OUT_DTG + p] + x, fma(m2a, K, s));
         }

@@ -65,40 +65,28 @@ __device__ __forceinline__ uint32_t out_of_ff_range(double x)
 }
 
 // hi + lo -> binary64 (truncated below the 53rd bit; error < 1 ulp).  Requires a normalised pair,
-// |lo| <= ulp(hi)/2, as produced by two_sum.
+// |lo| <= ulp(hi)/2, as produced by two_sum, and a finite hi (the callers' range checks guarantee it).
+// Branch-free; a zero hi gives a signed zero.
 __device__ __forceinline__ double merge_ff(ff v)
 {
     const uint32_t hb = __float_as_uint(v.hi), lb = __float_as_uint(v.lo);
     const uint32_t sign = hb & 0x80000000u;
     const uint32_t Eh = (hb >> 23) & 0xffu, El = (lb >> 23) & 0xffu;
-    if (Eh == 0u)                                          // zero (or a binary32 subnormal hi)
-        return __hiloint2double((int)sign, 0);
-    if (Eh == 255u)                                        // inf / nan
-        return __hiloint2double((int)(sign | 0x7ff00000u | ((hb & 0x7fffffu) >> 3)), 0);
     const uint32_t Mh = (hb & 0x7fffffu) | 0x800000u;
     const uint32_t Ml = (El != 0u) ? ((lb & 0x7fffffu) | 0x800000u) : 0u;
     const uint32_t d = Eh - El;                            // >= 24 for a normalised pair
     // lo aligned to the 29 low bits of the 53-bit significand
-    uint32_t L;
-    if (Ml == 0u || d >= 53u)
-        L = 0u;
-    else if (d <= 29u)
-        L = Ml << (29u - d);
-    else
-        L = Ml >> (d - 29u);
-    uint32_t hiM = Mh, loM = L;
-    if (L != 0u && ((hb ^ lb) & 0x80000000u)) {            // opposite signs: borrow from hi
-        hiM = Mh - 1u;
-        loM = (1u << 29) - L;
-    }
+    const uint32_t L = (d >= 53u) ? 0u : ((d <= 29u) ? (Ml << (29u - d)) : (Ml >> (d - 29u)));
+    const bool borrow = (L != 0u) && ((hb ^ lb) & 0x80000000u);   // opposite signs: borrow from hi
+    uint32_t hiM = borrow ? Mh - 1u : Mh;
+    uint32_t loM = borrow ? (1u << 29) - L : L;
     uint32_t E = Eh + (1023u - 127u);
-    if (hiM < 0x800000u) {                                 // hi was a power of two: renormalise
-        hiM = (hiM << 1) | (loM >> 28);
-        loM = (loM << 1) & 0x1fffffffu;
-        E -= 1u;
-    }
-    const uint32_t hw = sign | (E << 20) | ((hiM & 0x7fffffu) >> 3);
-    const uint32_t lw = ((hiM & 7u) << 29) | loM;
+    const bool renorm = hiM < 0x800000u;                   // hi was a power of two
+    hiM = renorm ? ((hiM << 1) | (loM >> 28)) : hiM;
+    loM = renorm ? ((loM << 1) & 0x1fffffffu) : loM;
+    E = renorm ? E - 1u : E;
+    const uint32_t hw = (Eh == 0u) ? sign : (sign | (E << 20) | ((hiM & 0x7fffffu) >> 3));
+    const uint32_t lw = (Eh == 0u) ? 0u : (((hiM & 7u) << 29) | loM);
     return __hiloint2double((int)hw, (int)lw);
 }
 

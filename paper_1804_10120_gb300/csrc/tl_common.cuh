@@ -35,36 +35,38 @@ template <typename T> __device__ __forceinline__ void st_stream(T *p, T v) { __s
 // ---- exact power-of-two scaling of binary64 on the integer pipe (the FP64 pipe is the scarce one) ----
 // half_exact(x) == x * 0.5 and twice_exact(x) == x * 2.0 in IEEE round-to-nearest-even for every
 // binary64 value, including zeros, subnormals, infinities and NaN.
+static __device__ __noinline__ double half_slow(double x) { return x * 0.5; }
+static __device__ __noinline__ double twice_slow(double x) { return x + x; }
+
+// The exponent field is adjusted with an inline-asm integer add on the high word, so that the compiler
+// cannot turn the bit manipulation back into an FP64 instruction; zeros are handled inline, other
+// operands without a normal result (subnormals, the smallest / largest normals, inf, nan) out of line.
 __device__ __forceinline__ double half_exact(double x)
 {
-    const uint64_t b = (uint64_t)__double_as_longlong(x);
-    const uint64_t sign = b & 0x8000000000000000ull, mag = b & 0x7fffffffffffffffull;
-    const uint64_t e = mag >> 52;
-    uint64_t r;
-    if (e > 1 && e < 2047)
-        r = mag - (1ull << 52);
-    else if (e == 2047)
-        r = mag;
-    else   // zero, subnormal or smallest normal: shift right, ties to even
-        r = (mag >> 1) + ((mag & 1) & ((mag >> 1) & 1));
-    return __longlong_as_double((long long)(sign | r));
+    const int hi = __double2hiint(x), lo = __double2loint(x);
+    const unsigned e = ((unsigned)hi >> 20) & 0x7ffu;
+    if (e - 2u < 2045u) {
+        int r;
+        asm("add.s32 %0, %1, -1048576;" : "=r"(r) : "r"(hi));
+        return __hiloint2double(r, lo);
+    }
+    if (((hi & 0x7fffffff) | lo) == 0)
+        return x;
+    return half_slow(x);
 }
 
 __device__ __forceinline__ double twice_exact(double x)
 {
-    const uint64_t b = (uint64_t)__double_as_longlong(x);
-    const uint64_t sign = b & 0x8000000000000000ull, mag = b & 0x7fffffffffffffffull;
-    const uint64_t e = mag >> 52;
-    uint64_t r;
-    if (e == 0)
-        r = mag << 1;                         // subnormal (or zero): exact, may become normal
-    else if (e < 2046)
-        r = mag + (1ull << 52);
-    else if (e == 2046)
-        r = 0x7ff0000000000000ull;            // overflow to infinity
-    else
-        r = mag;                              // inf / nan
-    return __longlong_as_double((long long)(sign | r));
+    const int hi = __double2hiint(x), lo = __double2loint(x);
+    const unsigned e = ((unsigned)hi >> 20) & 0x7ffu;
+    if (e - 1u < 2045u) {
+        int r;
+        asm("add.s32 %0, %1, 1048576;" : "=r"(r) : "r"(hi));
+        return __hiloint2double(r, lo);
+    }
+    if (((hi & 0x7fffffff) | lo) == 0)
+        return x;
+    return twice_slow(x);
 }
 
 // Out-of-line IEEE quotient for the rare operands outside the binary32 exponent range, kept out of the
@@ -99,6 +101,13 @@ __device__ __forceinline__ float f64_to_f32(double d, uint32_t &rare)
     const uint32_t inc = rb & ((sticky != 0u) | (t & 1u));
     const uint32_t r = ((t - 0xC0000000u) & 0x7fffffffu) + inc;       // a carry rounds into the exponent
     return __uint_as_float((zero ? 0u : r) | (hw & 0x80000000u));
+}
+
+// -x by flipping the sign bit on the integer pipe (for operands that would otherwise cost an FP64
+// instruction to negate).
+__device__ __forceinline__ double neg_exact(double x)
+{
+    return __hiloint2double(__double2hiint(x) ^ (int)0x80000000, __double2loint(x));
 }
 
 // ---- binary64 reciprocal ------------------------------------------------------------------------------
