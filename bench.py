@@ -4,7 +4,7 @@ A step is one pass of the fused forward chain (inverse metric -> Christoffel sym
 derivative of the shift -> d_t g_ij) over one grid of N = 2^24 (256^3) points with the seeded random
 grid recipe, all 43 inputs and 39 outputs resident in HBM.  The metric is grid points per second;
 achieved HBM GB/s counts the paper's effective bandwidth, 8 bytes x (43 + 39) components x N per pass
-(Eq. 22).  Inputs plus outputs (11 GB) exceed the 129 MB L2, so no flush is needed between steps.
+(Eq. 8).  Inputs plus outputs (11 GB) exceed the 129 MB L2, so no flush is needed between steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--variant f64|f64_ff|f32]
 
@@ -210,10 +210,30 @@ def reference_arm(args):
 
 # Algorithmic work per grid point (the design doc derives both):
 #   bytes: 8 x (43 + 39) for binary64, 4 x 82 for binary32 (each component array crosses HBM once);
-#   binary64 flops of the fused chain as this library formulates it (FMA = 2): inverse 35, Eq. 3 bracket
-#   18, Eq. 3 contraction 90, covariant shift derivative 54, Eq. 2 15.
+#   binary64 flops of the fused chain as this library formulates it (FMA = 2): inverse 35, Eq. 6 bracket
+#   18, Eq. 6 contraction 90, covariant shift derivative 54, Eq. 5 15.
 FLOPS_F64_PER_POINT = 212
 FP64_TFLOPS_PEAK = 2 * 2 * 152 * 2.07e9 / 1e12   # 2 DFMA / clk / SM x 2 flop x 152 SMs x 2070 MHz
+
+
+def _max_over_ranks(v, dev):
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(local_ms, points_per_rank, steps, world, max_over_ranks=None):
+    """Weak-scaling aggregate of independent per-rank grids: the job's time is the slowest rank's timed
+    region, its throughput all ranks' points over that time.  Returns (t_max_ms, points/s)."""
+    t_max = max_over_ranks(local_ms) if (world > 1 and max_over_ranks) else local_ms
+    return t_max, world * points_per_rank * steps / (t_max * 1e-3)
+
+
+def rank_seed(rank):
+    """Each rank times its own grid of the same recipe (seed 1 on rank 0)."""
+    return 1 + 1000 * rank
 
 
 def cuda_time(fn, steps, stream, warmup=3):
@@ -242,7 +262,7 @@ def extras(dev, stream, steps, x64, hbm):
     ms = cuda_time(lambda: tl.tl_dtg_forward(x64, y, dtype="f64_ff", stream=stream), steps, stream)
     out["f64_ff_forward"] = {"workload": "single grid N=2^24, seed 1", "ms": ms, "points_per_s": n / ms * 1e3,
                              "GB_s": 656 * n / ms / 1e6, "hbm_frac": 656 * n / ms / 1e6 / hbm,
-                             "arith": "binary64 inverse, Eq. 3 bracket and Eq. 2; float-float contractions"}
+                             "arith": "binary64 inverse, Eq. 6 bracket and Eq. 5; float-float contractions"}
     del y
     x32 = x64.float()
     y32 = torch.empty((39, n), dtype=torch.float32, device=dev)
@@ -265,8 +285,10 @@ def extras(dev, stream, steps, x64, hbm):
                       steps, stream)
     out["fwd_adjoint"] = {"workload": "N=2^22, seed 3, L = sum W dtg + V Gamma", "ms_forward": ms_f,
                           "ms_adjoint": ms_b, "ms": ms_fb, "points_per_s": n3 / ms_fb * 1e3,
-                          "GB_s": 1536 * n3 / ms_fb / 1e6, "hbm_frac": 1536 * n3 / ms_fb / 1e6 / hbm,
-                          "adjoint_GB_s": 880 * n3 / ms_b / 1e6}
+                          "GB_s": 1464 * n3 / ms_fb / 1e6, "hbm_frac": 1464 * n3 / ms_fb / 1e6 / hbm,
+                          "adjoint_GB_s": 808 * n3 / ms_b / 1e6,
+                          "bytes_per_point": "forward 656 + adjoint 808 (34 inputs: d_j beta_i is not needed, "
+                                             "24 upstream gradients, 43 input gradients)"}
     del x3, W, V, gout, y3, g3
     # batched: 600 subgrids n^3, n ~ U{8..48} (seed 2)
     sides = gridgen.subgrid_sides(600, 2)
@@ -373,7 +395,7 @@ def main():
     variant = args.variant
     td = torch.float32 if variant == "f32" else torch.float64
     esz = 4 if variant == "f32" else 8
-    x_host = gridgen.random_grid(n, 1 + 1000 * rank)
+    x_host = gridgen.random_grid(n, rank_seed(rank))
     x_pinned = torch.from_numpy(x_host).to(td).pin_memory()
     x = x_pinned.to(dev)
     y = torch.empty((39, n), dtype=td, device=dev)
@@ -399,12 +421,8 @@ def main():
         dist.barrier()
     per = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
     total_ms = ev[0].elapsed_time(ev[-1])
-    t_max = total_ms
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = world * n * args.steps / (t_max * 1e-3)
+    t_max, value = replica_throughput(total_ms, n, args.steps, world,
+                                      (lambda v: _max_over_ranks(v, dev)) if world > 1 else None)
     avg_launch_s = statistics.mean(per) * 1e-3
     hbm, peak_kind = peaks()
     bpp = BYTES_PER_POINT[variant]

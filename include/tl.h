@@ -4,19 +4,19 @@
  * At every point of an N-point grid the library evaluates, in one fused kernel, the chain of
  * Lewis & Pfeiffer, "Automatic generation of CUDA code performing tensor manipulations using C++
  * expression templates" (arXiv:1804.10120):
- *   1. g^ij, the inverse of the symmetric spatial metric g_ij (Sec. 1, after Eq. 3: "the inverse");
- *   2. the Christoffel symbols Gamma^i_jk = 1/2 g^il (d_k g_jl + d_j g_lk - d_l g_jk)   (Eq. 3);
+ *   1. g^ij, the inverse of the symmetric spatial metric g_ij (Sec. 1, after Eq. 6: "the inverse");
+ *   2. the Christoffel symbols Gamma^i_jk = 1/2 g^il (d_k g_jl + d_j g_lk - d_l g_jk)   (Eq. 6);
  *   3. the covariant derivative of the shift nabla_j beta_i = d_j beta_i - Gamma^k_ij beta_k
  *      (footnote to Listing 1);
- *   4. d_t g_ij = -2 alpha K_ij + nabla_i beta_j + nabla_j beta_i   (Eq. 2);
+ *   4. d_t g_ij = -2 alpha K_ij + nabla_i beta_j + nabla_j beta_i   (Eq. 5);
  * its adjoint (reverse-mode derivative; the paper has none), and a batched form that runs many
  * multi-domain subgrids (Sec. 1: "for multi-domain methods, on multiple spatial grids") in one launch.
  *
  * Data layout.  Structure of arrays: every tensor component is its own array of n elements (the
- * paper's Tensor<DataMesh>, Sec. 2), and a symmetric index pair is stored once (Sec. 2, lookup table).
+ * paper's Tensor<DataMesh>, Sec. 2.2), and a symmetric index pair is stored once (Sec. 2.2, lookup table).
  * Packed symmetric order p(i,j), i<=j:  (0,0)=0 (0,1)=1 (0,2)=2 (1,1)=3 (1,2)=4 (2,2)=5.
  *   inputs   g[p] = g_ij;  dg[3p+k] = d_k g_ij (derivative index innermost, as dg(i,j)(k) in
- *            Listing 4);  K[p] = K_ij;  alpha;  beta[i] = beta_i;  dbeta[3i+j] = d_j beta_i
+ *            Listing 3);  K[p] = K_ij;  alpha;  beta[i] = beta_i;  dbeta[3i+j] = d_j beta_i
  *   outputs  ginv[p] = g^ij;  gamma[6i + p(j,k)] = Gamma^i_jk;  dbcov[3i+j] = nabla_j beta_i;
  *            dtg[p] = d_t g_ij
  * Every table entry is a DEVICE pointer unless the function says otherwise.  Element type: double
@@ -63,8 +63,8 @@ typedef enum {
 typedef enum {
     TL_F64 = 0,      /* binary64 storage; every arithmetic operation in IEEE binary64              */
     TL_F32 = 1,      /* binary32 storage and arithmetic; det(g) and the 3x3 inverse in binary64    */
-    TL_F64_FF = 2    /* binary64 storage; inverse, Eq. 3 bracket and Eq. 2 in binary64; the two
-                        contractions (raising Eq. 3 with g^il, and Gamma^k_ij beta_k) in float-float
+    TL_F64_FF = 2    /* binary64 storage; inverse, Eq. 6 bracket and Eq. 5 in binary64; the two
+                        contractions (raising Eq. 6 with g^il, and Gamma^k_ij beta_k) in float-float
                         arithmetic (pairs of binary32, >= 46 significant bits) on the FP32 pipes   */
 } tl_dtype;
 

@@ -5,8 +5,8 @@ this package.  The CUDA library never links or calls it, and the two share no co
 
 ``dtg_oracle.c`` is a plain per-point loop nest in IEEE binary64 (compiled without floating-point
 contraction) that follows, in order: the inverse metric (adjugate / determinant), the Christoffel
-symbols of Eq. 3, the covariant derivative of the shift (footnote to Listing 1), and the metric
-evolution equation Eq. 2 of Lewis & Pfeiffer, arXiv:1804.10120; plus the hand-derived adjoint.
+symbols of Eq. 6, the covariant derivative of the shift (footnote to Listing 1), and the metric
+evolution equation Eq. 5 of Lewis & Pfeiffer, arXiv:1804.10120; plus the hand-derived adjoint.
 
 Array layout: 43 input arrays (g[6], dg[18] with dg[3p+k] = d_k g_p, K[6], alpha, beta[3],
 dbeta[9] with dbeta[3i+j] = d_j beta_i) and 39 output arrays (ginv[6], gamma[18] with

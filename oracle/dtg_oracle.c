@@ -8,24 +8,24 @@
  * What it computes (Lewis & Pfeiffer, arXiv:1804.10120), one grid point at a time, in IEEE binary64,
  * compiled with floating-point contraction disabled:
  *   1. g^ij, the inverse of the symmetric 3x3 spatial metric g_ij (the paper only says "the inverse",
- *      Sec. 1 after Eq. 3).  Written out as adjugate / determinant, the determinant by first-row
+ *      Sec. 1 after Eq. 6).  Written out as adjugate / determinant, the determinant by first-row
  *      expansion.
- *   2. The Christoffel symbols of the second kind, Eq. 3:
+ *   2. The Christoffel symbols of the second kind, Eq. 6:
  *          Gamma^i_jk = 1/2 sum_l g^il (d_k g_jl + d_j g_lk - d_l g_jk),
- *      evaluated for all 27 (i,j,k) with the terms in the order Eq. 3 prints them.
+ *      evaluated for all 27 (i,j,k) with the terms in the order Eq. 6 prints them.
  *   3. The covariant derivative of the shift, the footnote to Listing 1 (Sec. 1):
  *          nabla_j beta_i = d_j beta_i - sum_k Gamma^k_ij beta_k.
- *   4. The metric evolution equation, Eq. 2:
+ *   4. The metric evolution equation, Eq. 5:
  *          d_t g_ij = -2 alpha K_ij + nabla_i beta_j + nabla_j beta_i.
  * and the reverse-mode derivative of any linear functional of the 39 outputs (the adjoint; the paper
  * has none), derived by hand from steps 1-4.
  *
- * Storage convention (the paper keeps one element per symmetric pair through a lookup table, Sec. 2,
+ * Storage convention (the paper keeps one element per symmetric pair through a lookup table, Sec. 2.2,
  * and fixes no order; this file fixes one):
  *   packed symmetric index p(i,j) for i<=j: (0,0)->0 (0,1)->1 (0,2)->2 (1,1)->3 (1,2)->4 (2,2)->5.
  *   Input table (43 arrays of n doubles):
  *     [0..5]   g[p]            g_ij
- *     [6..23]  dg[3*p+k]       d_k g_ij  (derivative index innermost, as dg(i,j)(k) in Listing 4)
+ *     [6..23]  dg[3*p+k]       d_k g_ij  (derivative index innermost, as dg(i,j)(k) in Listing 3)
  *     [24..29] K[p]            K_ij
  *     [30]     alpha
  *     [31..33] beta[i]         beta_i
@@ -62,7 +62,7 @@ typedef struct {
 typedef struct {
     double det;
     double H[3][3];       /* g^ij                        */
-    double T[3][3][3];    /* T[l][j][k] = d_k g_jl + d_j g_lk - d_l g_jk (the bracket of Eq. 3) */
+    double T[3][3][3];    /* T[l][j][k] = d_k g_jl + d_j g_lk - d_l g_jk (the bracket of Eq. 6) */
     double Gam[3][3][3];  /* Gamma^i_jk                  */
     double Nb[3][3];      /* Nb[i][j] = nabla_j beta_i   */
     double dtg[3][3];     /* d_t g_ij (all 9, symmetric up to rounding) */
@@ -106,7 +106,7 @@ static void forward_point(const point_in *P, point_out *R)
     /* 1. inverse metric */
     inverse(P->G, &R->det, R->H);
 
-    /* 2. Christoffel symbols, Eq. 3, terms in printed order */
+    /* 2. Christoffel symbols, Eq. 6, terms in printed order */
     for (int l = 0; l < 3; ++l)
         for (int j = 0; j < 3; ++j)
             for (int k = 0; k < 3; ++k)
@@ -129,7 +129,7 @@ static void forward_point(const point_in *P, point_out *R)
             R->Nb[i][j] = P->B[i][j] - s;
         }
 
-    /* 4. Eq. 2: nabla_i beta_j = Nb[j][i], nabla_j beta_i = Nb[i][j] */
+    /* 4. Eq. 5: nabla_i beta_j = Nb[j][i], nabla_j beta_i = Nb[i][j] */
     for (int i = 0; i < 3; ++i)
         for (int j = 0; j < 3; ++j)
             R->dtg[i][j] = (-2.0 * P->alpha * P->Kc[i][j] + R->Nb[j][i]) + R->Nb[i][j];
@@ -179,13 +179,13 @@ int oracle_dtg_forward(const double *const in[ORACLE_N_IN], double *const out[OR
  * derivatives through both of its index orders.
  *
  * Derivation (reverse order of the forward steps, per point):
- *   Eq. 2     dtg_ij = -2 a K_ij + Nb[j][i] + Nb[i][j]   (i<=j stored)
+ *   Eq. 5     dtg_ij = -2 a K_ij + Nb[j][i] + Nb[i][j]   (i<=j stored)
  *               Kbar_ij = -2 a W_ij;  abar = -2 sum_{i<=j} W_ij K_ij;
  *               Nbar[i][j] += W, Nbar[j][i] += W  (once each for i<j; 2W on the diagonal)
  *   footnote  Nb[i][j] = B[i][j] - sum_k Gam[k][i][j] b[k]
  *               Bbar = Nbar;  bbar_k = -sum_ij Nbar[i][j] Gam[k][i][j];
  *               Gambar[k][i][j] += -Nbar[i][j] b[k]   (then folded onto the stored j<=k entries)
- *   Eq. 3     Gam[i][j][k] = 1/2 sum_l H[i][l] T[l][j][k]   (stored j<=k)
+ *   Eq. 6     Gam[i][j][k] = 1/2 sum_l H[i][l] T[l][j][k]   (stored j<=k)
  *               Hbar[i][l] += 1/2 sum_{j<=k} Gambar[i][jk] T[l][j][k];
  *               Tbar[l][jk] = 1/2 sum_i H[i][l] Gambar[i][jk]
  *             T[l][j][k] = D[j][l][k] + D[l][k][j] - D[j][k][l]
@@ -219,7 +219,7 @@ int oracle_dtg_backward(const double *const in[ORACLE_N_IN], const double *const
             for (int j = 0; j < 3; ++j)
                 Wnb[i][j] = gout[24 + 3 * i + j] ? gout[24 + 3 * i + j][x] : 0.0;
 
-        /* Eq. 2 */
+        /* Eq. 5 */
         double Kbar[6], abar = 0.0, Nbar[3][3];
         for (int i = 0; i < 3; ++i)
             for (int j = 0; j < 3; ++j)
@@ -253,7 +253,7 @@ int oracle_dtg_backward(const double *const in[ORACLE_N_IN], const double *const
                 for (int j = 0; j < 3; ++j)
                     Gambar[k][sym_index(i, j)] += -Nbar[i][j] * P.b[k];
 
-        /* Eq. 3 */
+        /* Eq. 6 */
         double Hbar[3][3], Tbar[3][6];
         for (int i = 0; i < 3; ++i)
             for (int l = 0; l < 3; ++l) {

@@ -1,4 +1,4 @@
-"""Effective-bandwidth accounting (Sec. 5.1, Eq. 22 of Lewis & Pfeiffer, arXiv:1804.10120).
+"""Effective-bandwidth accounting (Sec. 5.1, Eq. 8 of Lewis & Pfeiffer, arXiv:1804.10120).
 
 BW_eff = 8 bytes * (N_e * N + N_d) / t, where N is the number of grid points, N_e the number of distinct
 stored tensor elements an operation reads or writes, and N_d the number of doubles outside grid arrays.
@@ -77,9 +77,13 @@ def dtg_chain_refs():
 DTG_IN_ELEMENTS = 43
 DTG_OUT_ELEMENTS = 39
 DTG_ELEMENTS = DTG_IN_ELEMENTS + DTG_OUT_ELEMENTS
-# Adjoint alone: 43 inputs + the upstream gradients actually read + 43 input gradients written.
+# Adjoint alone: the inputs it reads (all but the 9 d_j beta_i, on which the gradient does not depend),
+# the upstream gradients actually read and the 43 input gradients written.
+ADJOINT_IN_ELEMENTS = DTG_IN_ELEMENTS - 9
+
+
 def adjoint_elements(n_upstream: int) -> int:
-    return DTG_IN_ELEMENTS + n_upstream + DTG_IN_ELEMENTS
+    return ADJOINT_IN_ELEMENTS + n_upstream + DTG_IN_ELEMENTS
 
 
 def bytes_per_point(elements: int, word: int = 8) -> int:

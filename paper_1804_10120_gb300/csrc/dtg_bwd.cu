@@ -1,7 +1,7 @@
 // dtg_bwd.cu -- adjoint of the fused chain: given upstream gradients of the 39 outputs, the gradient of
 // L = sum gout * out with respect to the 43 stored inputs.  The paper has no adjoint; this is the
-// reverse-mode derivative of Eq. 2, the footnote to Listing 1, Eq. 3 and the inverse metric, taken in
-// reverse order.  g^ij, the bracket T of Eq. 3 and Gamma are recomputed in registers from the inputs
+// reverse-mode derivative of Eq. 5, the footnote to Listing 1, Eq. 6 and the inverse metric, taken in
+// reverse order.  g^ij, the bracket T of Eq. 6 and Gamma are recomputed in registers from the inputs
 // (never stored or re-read), so one launch reads 43 inputs plus the upstream gradients present and
 // writes 43 input gradients.
 //
@@ -60,7 +60,7 @@ template <bool kU, bool kG> __device__ __forceinline__ void bwd_point_f64(const 
         for (int p = 0; p < 6; ++p)
             gam[i][p] = fma(h[sym(i, 2)], T[2][p], fma(h[sym(i, 1)], T[1][p], h[sym(i, 0)] * T[0][p]));
 
-    // ---- Eq. 2
+    // ---- Eq. 5
     const double alpha = ld_stream(a.in[IN_ALPHA] + x);
     const double m2a = -twice_exact(alpha);
     double W[6];
@@ -118,7 +118,7 @@ template <bool kU, bool kG> __device__ __forceinline__ void bwd_point_f64(const 
         for (int p = 0; p < 6; ++p)
             gbar[k][p] = fma(-beta[k], S[p], ld_opt(a.gout[OUT_GAMMA + 6 * k + p], x));
 
-    // ---- Eq. 3: Hbar (not symmetric) and Tbar
+    // ---- Eq. 6: Hbar (not symmetric) and Tbar
     double Hb[3][3];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
@@ -137,7 +137,7 @@ template <bool kU, bool kG> __device__ __forceinline__ void bwd_point_f64(const 
         for (int p = 0; p < 6; ++p)
             Tb[l][p] = fma(h[sym(2, l)], gbar[2][p], fma(h[sym(1, l)], gbar[1][p], h[sym(0, l)] * gbar[0][p]));
 
-    // ---- bracket -> d_k g_ij: every T_lp term of Eq. 3 scattered onto the stored derivative it reads
+    // ---- bracket -> d_k g_ij: every T_lp term of Eq. 6 scattered onto the stored derivative it reads
     double dgb[18];
 #pragma unroll
     for (int s = 0; s < 18; ++s)

@@ -1,9 +1,9 @@
-// dtg_fwd.cu -- fused forward kernels: inverse metric -> Christoffel symbols (Eq. 3) -> covariant
-// derivative of the shift (footnote to Listing 1) -> d_t g_ij (Eq. 2), one grid point per thread.
+// dtg_fwd.cu -- fused forward kernels: inverse metric -> Christoffel symbols (Eq. 6) -> covariant
+// derivative of the shift (footnote to Listing 1) -> d_t g_ij (Eq. 5), one grid point per thread.
 //
 // Each thread reads the 43 input components of its point once, keeps every intermediate in
 // registers and writes the 39 outputs once: 656 bytes of HBM traffic per point in binary64, the
-// paper's effective-bandwidth count N_e = 82 (Sec. 5.1, Eq. 22).  Unlike the paper's generated
+// paper's effective-bandwidth count N_e = 82 (Sec. 5.1, Eq. 8).  Unlike the paper's generated
 // kernels (one thread per point and output component, one kernel per expression, pointer tables
 // read from global memory; Sec. 4), the whole chain is one kernel and the pointer tables are kernel
 // parameters.
@@ -70,7 +70,7 @@ __device__ __forceinline__ bool fwd_point_f32(const FwdArgs<float> &a, int64_t x
     for (int p = 0; p < 6; ++p)
         st_stream(a.out[OUT_GINV + p] + x, gi[p]);
 
-    // step 2: Eq. 3
+    // step 2: Eq. 6
     float dg[18];
 #pragma unroll
     for (int s = 0; s < 18; ++s)
@@ -98,7 +98,7 @@ __device__ __forceinline__ bool fwd_point_f32(const FwdArgs<float> &a, int64_t x
             st_stream(a.out[OUT_DBCOV + 3 * i + j] + x, nb[i][j]);
         }
 
-    // step 4: Eq. 2
+    // step 4: Eq. 5
     const float m2a = -2.0f * v[IN_ALPHA];
 #pragma unroll
     for (int i = 0; i < 3; ++i)

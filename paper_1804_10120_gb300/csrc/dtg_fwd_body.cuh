@@ -5,7 +5,7 @@
 
 namespace tl {
 
-// The bracket of Eq. 3 for the stored pairs, T[l][p(j,k)] = d_k g_jl + d_j g_lk - d_l g_jk, from
+// The bracket of Eq. 6 for the stored pairs, T[l][p(j,k)] = d_k g_jl + d_j g_lk - d_l g_jk, from
 // D(a,b,c) = d_c g_ab.  When l is one of j, k two terms cancel identically:
 //   l == j: T = d_k g_jj;   l == k: T = d_j g_kk;   j == k != l: T = 2 d_j g_jl - d_l g_jj.
 // Only the three (j<k, l outside {j,k}) entries need the full three-term sum.
@@ -68,11 +68,11 @@ __device__ __forceinline__ void fwd_point_f64(const FwdArgs<double> &a, int64_t 
 #pragma unroll
     for (int p = 0; p < 6; ++p) {
         ginv[p] = c[p] * rdet;
-        h[p] = half_exact(ginv[p]);          // 1/2 g^il of Eq. 3
+        h[p] = half_exact(ginv[p]);          // 1/2 g^il of Eq. 6
         st_stream(a.out[OUT_GINV + p] + x, ginv[p]);
     }
 
-    // step 2: Christoffel symbols, Eq. 3
+    // step 2: Christoffel symbols, Eq. 6
     double T[3][6];
     christoffel_bracket<double>(dg, T);
     double gam[3][6];
@@ -98,7 +98,7 @@ __device__ __forceinline__ void fwd_point_f64(const FwdArgs<double> &a, int64_t 
             st_stream(a.out[OUT_DBCOV + 3 * i + j] + x, nb[i][j]);
         }
 
-    // step 4: Eq. 2, d_t g_ij = -2 alpha K_ij + nabla_i beta_j + nabla_j beta_i
+    // step 4: Eq. 5, d_t g_ij = -2 alpha K_ij + nabla_i beta_j + nabla_j beta_i
     const double m2a = neg_exact(twice_exact(v[IN_ALPHA]));
 #pragma unroll
     for (int i = 0; i < 3; ++i)

@@ -3,8 +3,8 @@
 // GB300 issues FP64 arithmetic at 1/64 of its FP32 rate (two FP64 operations per clock per SM), and
 // the all-binary64 chain needs ~126 of them per point: that alone caps it near 45 % of the HBM
 // roofline.  This kernel keeps binary64 hardware for the cancellation-prone parts -- the cofactors,
-// determinant and inverse of g_ij, the bracket of Eq. 3 and Eq. 2 itself -- and evaluates the two
-// contractions, Gamma^i_jk = sum_l (g^il / 2) T_ljk (Eq. 3) and sum_k Gamma^k_ij beta_k (footnote to
+// determinant and inverse of g_ij, the bracket of Eq. 6 and Eq. 5 itself -- and evaluates the two
+// contractions, Gamma^i_jk = sum_l (g^il / 2) T_ljk (Eq. 6) and sum_k Gamma^k_ij beta_k (footnote to
 // Listing 1), in float-float pairs on the FP32 pipes, converting between binary64 and pairs with
 // integer operations (ff.cuh).  FP64 work drops to ~54 operations per point.  Points whose values
 // fall outside the pair format's safe range (|x| >= 2^63, inf, nan) are evaluated by the
@@ -56,7 +56,7 @@ __device__ __forceinline__ void fwd_point_ff(const FwdArgs<double> &a, int64_t x
         h[p] = split_ff(half_exact(gi), big);
     }
 
-    // bracket of Eq. 3 in binary64, then pairs
+    // bracket of Eq. 6 in binary64, then pairs
     double Td[3][6];
     christoffel_bracket<double>(dg, Td);
     ff T[3][6];
@@ -75,7 +75,7 @@ __device__ __forceinline__ void fwd_point_ff(const FwdArgs<double> &a, int64_t x
         return;
     }
 
-    // step 2: Eq. 3 contraction in pairs
+    // step 2: Eq. 6 contraction in pairs
     ff gam[3][6];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
@@ -100,7 +100,7 @@ __device__ __forceinline__ void fwd_point_ff(const FwdArgs<double> &a, int64_t x
             st_stream(a.out[OUT_DBCOV + 3 * i + j] + x, nb[i][j]);
         }
 
-    // step 4: Eq. 2 in binary64
+    // step 4: Eq. 5 in binary64
     const double m2a = neg_exact(twice_exact(v[IN_ALPHA]));
 #pragma unroll
     for (int i = 0; i < 3; ++i)

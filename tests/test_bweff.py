@@ -1,4 +1,4 @@
-"""Element counts of the effective-bandwidth metric (Sec. 5.1, Eq. 22) against the paper's worked
+"""Element counts of the effective-bandwidth metric (Sec. 5.1, Eq. 8) against the paper's worked
 examples, and the count used for the fused chain."""
 import os
 
@@ -29,3 +29,8 @@ def test_paper_examples():
 
 def test_fused_chain_count():
     assert count_elements(dtg_chain_refs(), {"i": 3, "j": 3, "k": 3}) == DTG_ELEMENTS == 82
+
+
+def test_adjoint_element_count():
+    from paper_1804_10120_gb300.bweff import adjoint_elements
+    assert adjoint_elements(24) == 34 + 24 + 43 == 101

@@ -1,0 +1,64 @@
+"""The multi-rank (torchrun) form of the benchmark: independent grids per rank, no collective on the
+data path, job time = max over ranks.  Checked with two gloo ranks on the CPU."""
+import os
+import socket
+
+import pytest
+
+torch = pytest.importorskip("torch")
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _worker(rank, world, port, q):
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import torch.distributed as dist
+    import bench
+    import gridgen
+    import oracle
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+
+    def max_over(v):
+        t = torch.tensor([v], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    local_ms = 10.0 * (rank + 1)          # rank 1 is the slow one
+    t_max, value = bench.replica_throughput(local_ms, 1000, 4, world, max_over)
+    # each rank's grid is its own and the oracle runs on it without any exchange
+    x = gridgen.random_grid(64, bench.rank_seed(rank))
+    y = oracle.forward(x)
+    q.put((rank, t_max, value, float(x[0, 0]), float(y[33, 0])))
+    dist.destroy_process_group()
+
+
+def test_two_rank_replicas_weak_scaling():
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    (r0, t0, v0, x0, y0), (r1, t1, v1, x1, y1) = res
+    assert t0 == t1 == 20.0                          # max over ranks
+    assert v0 == v1 == 2 * 1000 * 4 / 20e-3          # all ranks' points over the slowest time
+    assert x0 != x1 and y0 != y1                     # independent grids
+
+
+def test_single_rank_is_plain_throughput():
+    import bench
+    t, v = bench.replica_throughput(8.0, 2 ** 24, 10, 1)
+    assert t == 8.0 and v == 2 ** 24 * 10 / 8e-3

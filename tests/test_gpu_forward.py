@@ -13,7 +13,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 # Binary32 form.  Computation error alone (oracle evaluated on the binary32-rounded inputs): the chain
-# is at most ~6 dependent roundings deep (bracket 2, raise 3, covariant derivative 3, Eq. 2 2) and each
+# is at most ~6 dependent roundings deep (bracket 2, raise 3, covariant derivative 3, Eq. 5 2) and each
 # output is a short sum whose terms are bounded by its component's maximum, so a normwise error of a
 # few tens of ulp(2^-24 = 6e-8) bounds it: 2e-6.  End to end against the binary64 inputs the storage
 # rounding of the 43 inputs (relative 2^-24 each) enters with the same conditioning: 5e-6.

@@ -249,7 +249,7 @@ def test_curvilinear_flat_space_closed_forms():
 
 def test_killing_field_rotation():
     """A rigid rotation of flat space is a Killing field: nabla_i beta_j + nabla_j beta_i = 0, so
-    d_t g_ij = -2 alpha K_ij (Eq. 2)."""
+    d_t g_ij = -2 alpha K_ij (Eq. 5)."""
     n = 300
     rng = np.random.default_rng(9)
     C = rng.uniform(-0.05, 0.05, size=(3, 3, 3, n)); C = 0.5 * (C + C.transpose(0, 2, 1, 3))
