@@ -96,12 +96,17 @@ TL_API tl_status tl_dtg_backward(const tl_dtg_in *in, const tl_dtg_gout *gout, c
 
 /*
  * Forward with HOST arrays (end-to-end form): copies the 43 input arrays host->device into `workspace`,
- * runs tl_dtg_forward there and copies the 39 outputs device->host, all enqueued on `stream`, in
- * chunks so that copies in both directions overlap the kernel.  `in` and `out` hold HOST pointers
- * (page-locked memory gives full copy bandwidth; pageable memory works but the copies then
- * synchronise).  `workspace` is a DEVICE buffer of at least tl_dtg_host_workspace_bytes(n, dtype)
- * bytes owned by the caller.  Returns after enqueueing; the host outputs are valid once `stream`
- * completes.
+ * runs the forward kernel there and copies the 39 outputs device->host.  The work is cut into chunks of
+ * 2^19 points that flow through three library-owned streams (host->device copies, kernel,
+ * device->host copies) over three workspace slots, so both copy directions and the kernel overlap; the
+ * streams fork from and join back into `stream`, so the host outputs are valid once `stream` reaches
+ * the join.  When a table's arrays are equally spaced (one [43, n] or [39, n] host array) each chunk
+ * moves with a single 2-D copy.  `in` and `out` hold HOST pointers (page-locked memory gives full
+ * copy bandwidth; pageable memory works, but the copies then synchronise with the host).
+ * `workspace` is a DEVICE buffer of at least tl_dtg_host_workspace_bytes(n, dtype) bytes
+ * (at most 3 x 82 x 2^19 elements) owned by the caller.  The first call on a device creates the three
+ * streams and their events, which live until exit; concurrent calls on one device are serialised on
+ * the host while they enqueue.
  */
 TL_API size_t tl_dtg_host_workspace_bytes(int64_t n, tl_dtype dtype);
 TL_API tl_status tl_dtg_forward_host(const tl_dtg_in *in, const tl_dtg_out *out, int64_t n, tl_dtype dtype,

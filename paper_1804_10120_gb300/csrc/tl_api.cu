@@ -196,39 +196,88 @@ tl_status check_forward(const tl_dtg_in *in, const tl_dtg_out *out, int64_t n, t
 }
 
 // ---- host-buffer pipeline ----------------------------------------------------------------------------
-constexpr int64_t kHostChunk = int64_t(1) << 20;   // points per pipeline chunk
-constexpr int kHostLanes = 2;                      // chunks in flight (double buffering)
+// Chunks of kHostChunk points flow through three streams -- host->device copies, kernel, device->host
+// copies -- over kHostSlots workspace slots, so that both copy directions and the kernel overlap.
+constexpr int64_t kHostChunk = int64_t(1) << 19;   // points per pipeline chunk
+constexpr int kHostSlots = 3;
 
-struct HostLanes {
+struct HostPipe {
     std::mutex mu;
     bool ready = false;
-    cudaStream_t s[kHostLanes] = {};
-    cudaEvent_t fork = nullptr, join[kHostLanes] = {};
+    cudaStream_t h2d = nullptr, cmp = nullptr, d2h = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+    cudaEvent_t in_ready[kHostSlots] = {}, done[kHostSlots] = {}, slot_free[kHostSlots] = {};
 };
-HostLanes g_lanes[kMaxDevices];
-std::mutex g_lanes_mu;
+HostPipe g_pipes[kMaxDevices];
+std::mutex g_pipes_mu;
 
-tl_status host_lanes(HostLanes **out)
+tl_status host_pipe(HostPipe **out)
 {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess)
         return cuda_fail(e, "cudaGetDevice");
-    std::lock_guard<std::mutex> lk(g_lanes_mu);
-    HostLanes &L = g_lanes[dev];
-    if (!L.ready) {
-        for (int i = 0; i < kHostLanes; ++i) {
-            if ((e = cudaStreamCreateWithFlags(&L.s[i], cudaStreamNonBlocking)) != cudaSuccess)
+    std::lock_guard<std::mutex> lk(g_pipes_mu);
+    HostPipe &P = g_pipes[dev];
+    if (!P.ready) {
+        cudaStream_t *ss[3] = {&P.h2d, &P.cmp, &P.d2h};
+        for (cudaStream_t *sp : ss)
+            if ((e = cudaStreamCreateWithFlags(sp, cudaStreamNonBlocking)) != cudaSuccess)
                 return cuda_fail(e, "cudaStreamCreateWithFlags");
-            if ((e = cudaEventCreateWithFlags(&L.join[i], cudaEventDisableTiming)) != cudaSuccess)
-                return cuda_fail(e, "cudaEventCreateWithFlags");
+        cudaEvent_t *es[2 + 3 * kHostSlots];
+        int k = 0;
+        es[k++] = &P.fork;
+        es[k++] = &P.join;
+        for (int i = 0; i < kHostSlots; ++i) {
+            es[k++] = &P.in_ready[i];
+            es[k++] = &P.done[i];
+            es[k++] = &P.slot_free[i];
         }
-        if ((e = cudaEventCreateWithFlags(&L.fork, cudaEventDisableTiming)) != cudaSuccess)
-            return cuda_fail(e, "cudaEventCreateWithFlags");
-        L.ready = true;
+        for (int i = 0; i < k; ++i)
+            if ((e = cudaEventCreateWithFlags(es[i], cudaEventDisableTiming)) != cudaSuccess)
+                return cuda_fail(e, "cudaEventCreateWithFlags");
+        P.ready = true;
     }
-    *out = &L;
+    *out = &P;
     return TL_OK;
+}
+
+// The byte stride between consecutive arrays of a table if it is uniform (a [count, n] array), else 0.
+size_t uniform_stride(const char *const *p, int count, size_t row_bytes)
+{
+    const intptr_t st = (intptr_t)(p[1] - p[0]);
+    if (st < (intptr_t)row_bytes)
+        return 0;
+    for (int q = 2; q < count; ++q)
+        if ((intptr_t)(p[q] - p[q - 1]) != st)
+            return 0;
+    return (size_t)st;
+}
+
+// Copies of m points of a table between host arrays (offset x0) and a slot's contiguous rows.  With a
+// uniform host stride the rows move as one 2-D copy; equally spaced arrays may still be separate
+// allocations, which the runtime rejects for a 2-D copy (invalid value): then *hstride is cleared and
+// the rows are copied one by one from here on.
+cudaError_t copy_table(char *const *host, int count, int64_t x0, int64_t m, char *slot, int64_t chunk, size_t esz,
+                       size_t *hstride, bool to_device, cudaStream_t st)
+{
+    const cudaMemcpyKind kind = to_device ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost;
+    if (*hstride) {
+        char *h = host[0] + x0 * esz;
+        const cudaError_t e = to_device ? cudaMemcpy2DAsync(slot, chunk * esz, h, *hstride, m * esz, count, kind, st)
+                                        : cudaMemcpy2DAsync(h, *hstride, slot, chunk * esz, m * esz, count, kind, st);
+        if (e != cudaErrorInvalidValue)
+            return e;
+        (void)cudaGetLastError();   // not sticky; fall back to one copy per array
+        *hstride = 0;
+    }
+    for (int q = 0; q < count; ++q) {
+        char *h = host[q] + x0 * esz, *d = slot + (size_t)q * chunk * esz;
+        const cudaError_t e = to_device ? cudaMemcpyAsync(d, h, m * esz, kind, st) : cudaMemcpyAsync(h, d, m * esz, kind, st);
+        if (e != cudaSuccess)
+            return e;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace tl
@@ -309,8 +358,8 @@ size_t tl_dtg_host_workspace_bytes(int64_t n, tl_dtype dtype)
     if (n <= 0 || !dtype_ok(dtype))
         return 0;
     const int64_t chunk = std::min<int64_t>(n, kHostChunk);
-    const int64_t lanes = std::min<int64_t>(kHostLanes, (n + chunk - 1) / chunk);
-    return (size_t)(lanes * (N_IN + N_OUT) * chunk) * elem_size(dtype);
+    const int64_t slots = std::min<int64_t>(kHostSlots, (n + chunk - 1) / chunk);
+    return (size_t)(slots * (N_IN + N_OUT) * chunk) * elem_size(dtype);
 }
 
 tl_status tl_dtg_forward_host(const tl_dtg_in *in, const tl_dtg_out *out, int64_t n, tl_dtype dtype,
@@ -327,53 +376,57 @@ tl_status tl_dtg_forward_host(const tl_dtg_in *in, const tl_dtg_out *out, int64_
     const DeviceInfo *d = nullptr;
     if ((s = device_info(&d)) != TL_OK)
         return s;
-    HostLanes *L = nullptr;
-    if ((s = host_lanes(&L)) != TL_OK)
+    HostPipe *P = nullptr;
+    if ((s = host_pipe(&P)) != TL_OK)
         return s;
-    // the lanes and their events are shared per device: one caller enqueues at a time
-    std::lock_guard<std::mutex> enqueue_lock(L->mu);
+    // the pipeline's streams and events are shared per device: one caller enqueues at a time
+    std::lock_guard<std::mutex> enqueue_lock(P->mu);
     const size_t esz = elem_size(dtype);
     const int64_t chunk = std::min<int64_t>(n, kHostChunk);
     const cudaStream_t user = (cudaStream_t)stream;
-    cudaError_t e;
-    if ((e = cudaEventRecord(L->fork, user)) != cudaSuccess)
-        return cuda_fail(e, "cudaEventRecord");
-    for (int i = 0; i < kHostLanes; ++i)
-        if ((e = cudaStreamWaitEvent(L->s[i], L->fork, 0)) != cudaSuccess)
-            return cuda_fail(e, "cudaStreamWaitEvent");
-    const char *const *hin = (const char *const *)in;
+    char *const *hin = (char *const *)in;
     char *const *hout = (char *const *)out;
+    size_t sin = uniform_stride(hin, N_IN, n * esz), sout = uniform_stride(hout, N_OUT, n * esz);
+    cudaError_t e;
+    if ((e = cudaEventRecord(P->fork, user)) != cudaSuccess)
+        return cuda_fail(e, "cudaEventRecord");
+    for (cudaStream_t st : {P->h2d, P->cmp, P->d2h})
+        if ((e = cudaStreamWaitEvent(st, P->fork, 0)) != cudaSuccess)
+            return cuda_fail(e, "cudaStreamWaitEvent");
     int64_t c = 0;
     for (int64_t x0 = 0; x0 < n; x0 += chunk, ++c) {
-        const int lane = (int)(c % kHostLanes);
-        const cudaStream_t st = L->s[lane];
+        const int b = (int)(c % kHostSlots);
         const int64_t m = std::min(chunk, n - x0);
-        char *base = (char *)workspace + (size_t)lane * (N_IN + N_OUT) * chunk * esz;
+        char *base = (char *)workspace + (size_t)b * (N_IN + N_OUT) * chunk * esz;
+        char *slot_in = base, *slot_out = base + (size_t)N_IN * chunk * esz;
+        if (c >= kHostSlots && (e = cudaStreamWaitEvent(P->h2d, P->slot_free[b], 0)) != cudaSuccess)
+            return cuda_fail(e, "cudaStreamWaitEvent");
+        if ((e = copy_table((char *const *)hin, N_IN, x0, m, slot_in, chunk, esz, &sin, true, P->h2d)) != cudaSuccess)
+            return cuda_fail(e, "host->device copy");
+        if ((e = cudaEventRecord(P->in_ready[b], P->h2d)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(P->cmp, P->in_ready[b], 0)) != cudaSuccess)
+            return cuda_fail(e, "pipeline event");
         tl_dtg_in din;
         tl_dtg_out dout;
         const void **dinp = (const void **)&din;
         void **doutp = (void **)&dout;
-        for (int q = 0; q < N_IN; ++q) {
-            dinp[q] = base + (size_t)q * chunk * esz;
-            if ((e = cudaMemcpyAsync((void *)dinp[q], hin[q] + x0 * esz, m * esz, cudaMemcpyHostToDevice, st)) !=
-                cudaSuccess)
-                return cuda_fail(e, "cudaMemcpyAsync host->device");
-        }
+        for (int q = 0; q < N_IN; ++q)
+            dinp[q] = slot_in + (size_t)q * chunk * esz;
         for (int q = 0; q < N_OUT; ++q)
-            doutp[q] = base + (size_t)(N_IN + q) * chunk * esz;
-        if ((s = launch_forward(*d, &din, &dout, m, dtype, st)) != TL_OK)
+            doutp[q] = slot_out + (size_t)q * chunk * esz;
+        if ((s = launch_forward(*d, &din, &dout, m, dtype, P->cmp)) != TL_OK)
             return s;
-        for (int q = 0; q < N_OUT; ++q)
-            if ((e = cudaMemcpyAsync(hout[q] + x0 * esz, doutp[q], m * esz, cudaMemcpyDeviceToHost, st)) !=
-                cudaSuccess)
-                return cuda_fail(e, "cudaMemcpyAsync device->host");
-    }
-    for (int i = 0; i < kHostLanes; ++i) {
-        if ((e = cudaEventRecord(L->join[i], L->s[i])) != cudaSuccess)
+        if ((e = cudaEventRecord(P->done[b], P->cmp)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(P->d2h, P->done[b], 0)) != cudaSuccess)
+            return cuda_fail(e, "pipeline event");
+        if ((e = copy_table(hout, N_OUT, x0, m, slot_out, chunk, esz, &sout, false, P->d2h)) != cudaSuccess)
+            return cuda_fail(e, "device->host copy");
+        if ((e = cudaEventRecord(P->slot_free[b], P->d2h)) != cudaSuccess)
             return cuda_fail(e, "cudaEventRecord");
-        if ((e = cudaStreamWaitEvent(user, L->join[i], 0)) != cudaSuccess)
-            return cuda_fail(e, "cudaStreamWaitEvent");
     }
+    // the last device->host copy follows every earlier operation of the pipeline
+    if ((e = cudaEventRecord(P->join, P->d2h)) != cudaSuccess || (e = cudaStreamWaitEvent(user, P->join, 0)) != cudaSuccess)
+        return cuda_fail(e, "pipeline join");
     return TL_OK;
 }
 

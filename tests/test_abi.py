@@ -89,7 +89,8 @@ def test_host_workspace_size(L):
     assert L.tl_dtg_host_workspace_bytes(100, 0) == 100 * 82 * 8
     assert L.tl_dtg_host_workspace_bytes(100, 1) == 100 * 82 * 4
     big = 1 << 24
-    assert L.tl_dtg_host_workspace_bytes(big, 0) == 2 * (1 << 20) * 82 * 8
+    assert L.tl_dtg_host_workspace_bytes(big, 0) == 3 * (1 << 19) * 82 * 8
+    assert L.tl_dtg_host_workspace_bytes((1 << 19) + 1, 1) == 2 * (1 << 19) * 82 * 4
 
 
 def test_batched_prepare_argument_checks(L):

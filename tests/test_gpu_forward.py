@@ -148,6 +148,28 @@ def test_host_buffer_entry_point():
     assert_components(y[:, idx], oracle.forward(np.ascontiguousarray(x[:, idx])), TOL_F64, what="host path")
 
 
+def test_host_entry_point_separate_arrays_and_f32():
+    """Host tables whose arrays are separate allocations (per-array copies), binary32, n spanning four
+    chunks with a ragged tail, called twice in a row on a non-default stream."""
+    import paper_1804_10120_gb300 as tl
+    n = 3 * (1 << 19) + 777
+    x = gridgen.random_grid(n, 9).astype(np.float32)
+    ins = [torch.from_numpy(x[s].copy()).pin_memory() for s in range(43)]
+    outs = [torch.empty(n, dtype=torch.float32).pin_memory() for _ in range(39)]
+    st = torch.cuda.Stream()
+    for _ in range(2):
+        for o in outs:
+            o.fill_(float("nan"))
+        tl.tl_dtg_forward_host(ins, outs, dtype="f32", stream=st)
+        st.synchronize()
+        y = np.stack([o.numpy() for o in outs]).astype(np.float64)
+        rng = np.random.default_rng(9)
+        idx = np.unique(np.concatenate([np.arange(1000), np.arange(n - 1000, n), rng.integers(0, n, 20000)]))
+        err = component_errors(y[:, idx], oracle.forward(np.ascontiguousarray(x[:, idx].astype(np.float64))))
+        assert err.max() <= TOL_F32_COMPUTE
+        assert not np.isnan(y).any()
+
+
 def test_device_check_rejects_nothing_on_sm103():
     import paper_1804_10120_gb300 as tl
     assert torch.cuda.get_device_capability(0) == (10, 3)
