@@ -12,7 +12,7 @@
 
 namespace tl {
 
-__global__ void __launch_bounds__(kFwdThreads) dtg_fwd_f64_kernel(const FwdArgs<double> a, int64_t n)
+__global__ void __launch_bounds__(kFwdThreads, 2) dtg_fwd_f64_kernel(const FwdArgs<double> a, int64_t n)
 {
     const GridStride gs;
     for (int64_t x = gs.first; x < n; x += gs.step)
