@@ -283,6 +283,13 @@ def extras(dev, stream, steps, x64, hbm):
     ms_b = cuda_time(lambda: tl.tl_dtg_backward(x3, gout, g3, stream=stream), steps, stream)
     ms_fb = cuda_time(lambda: (tl.tl_dtg_forward(x3, y3, stream=stream), tl.tl_dtg_backward(x3, gout, g3, stream=stream)),
                       steps, stream)
+    ms_fb_ff = cuda_time(lambda: (tl.tl_dtg_forward(x3, y3, dtype="f64_ff", stream=stream),
+                                  tl.tl_dtg_backward(x3, gout, g3, dtype="f64_ff", stream=stream)), steps, stream)
+    ms_b_ff = cuda_time(lambda: tl.tl_dtg_backward(x3, gout, g3, dtype="f64_ff", stream=stream), steps, stream)
+    out["fwd_adjoint_ff"] = {"workload": "N=2^22, seed 3, L = sum W dtg + V Gamma", "ms_adjoint": ms_b_ff,
+                             "ms": ms_fb_ff, "points_per_s": n3 / ms_fb_ff * 1e3, "GB_s": 1464 * n3 / ms_fb_ff / 1e6,
+                             "hbm_frac": 1464 * n3 / ms_fb_ff / 1e6 / hbm,
+                             "arith": "float-float forward and adjoint (binary64 inverse, bracket, folds)"}
     out["fwd_adjoint"] = {"workload": "N=2^22, seed 3, L = sum W dtg + V Gamma", "ms_forward": ms_f,
                           "ms_adjoint": ms_b, "ms": ms_fb, "points_per_s": n3 / ms_fb * 1e3,
                           "GB_s": 1464 * n3 / ms_fb / 1e6, "hbm_frac": 1464 * n3 / ms_fb / 1e6 / hbm,
@@ -352,7 +359,8 @@ def only_form(args):
         V = torch.from_numpy(gridgen.normal_fields(18, n, 3, 1100)).to(dev)
         gout = [None] * 6 + [V[i] for i in range(18)] + [None] * 9 + [W[i] for i in range(6)]
         g = torch.empty((43, n), dtype=torch.float64, device=dev)
-        fn = lambda: tl.tl_dtg_backward(x, gout, g, stream=stream)
+        adj_dtype = "f64_ff" if args.variant == "f64_ff" else "f64"
+        fn = lambda: tl.tl_dtg_backward(x, gout, g, dtype=adj_dtype, stream=stream)
         units = n
     else:
         sides = gridgen.subgrid_sides(args.grids, 2)

@@ -88,8 +88,10 @@ TL_API tl_status tl_dtg_forward(const tl_dtg_in *in, const tl_dtg_out *out, int6
 /*
  * Adjoint: with L = sum over points and outputs of gout * out, writes dL/d(input) for every stored
  * input element into gin.  A symmetric input stored once receives the sum over both index orders.
- * g^ij and Gamma are recomputed from the inputs, not read.  Same rules as tl_dtg_forward; gin must
- * not overlap in or gout.
+ * g^ij and Gamma are recomputed from the inputs, not read; d_j beta_i is never read (the gradient
+ * does not depend on it).  TL_F64: binary64 throughout; TL_F64_FF: binary64 inverse, bracket and
+ * the Eq. 5 terms, every contraction in float-float pairs; TL_F32: not provided
+ * (TL_ERR_UNSUPPORTED).  Same rules as tl_dtg_forward; gin must not overlap in or gout.
  */
 TL_API tl_status tl_dtg_backward(const tl_dtg_in *in, const tl_dtg_gout *gout, const tl_dtg_gin *gin, int64_t n,
                           tl_dtype dtype, tl_stream stream);

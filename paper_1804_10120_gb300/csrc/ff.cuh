@@ -112,6 +112,61 @@ __device__ __forceinline__ ff dot3_ff(const ff &a0, const ff &b0, const ff &a1, 
     return r;
 }
 
+// Accumulator for sums of pair products: s collects the leading products with TwoSum, lo every
+// low-order part (TwoProduct errors, cross terms, TwoSum errors) in binary32.
+struct ffacc {
+    float s, lo;
+};
+
+// The exact leading product a.hi*b.hi and the low-order part of a*b (TwoProduct error plus the two
+// cross terms; the lo*lo term, below 2^-48 |a b|, is dropped).
+__device__ __forceinline__ void ff_prod(const ff &a, const ff &b, float &p, float &q)
+{
+    p = __fmul_rn(a.hi, b.hi);
+    q = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, __fmaf_rn(a.hi, b.hi, -p)));
+}
+
+__device__ __forceinline__ ffacc acc_from(const ff &c) { return ffacc{c.hi, c.lo}; }
+
+__device__ __forceinline__ ffacc acc_prod(const ff &a, const ff &b)
+{
+    ffacc A;
+    ff_prod(a, b, A.s, A.lo);
+    return A;
+}
+
+// A += a * b
+__device__ __forceinline__ void acc_add_prod(ffacc &A, const ff &a, const ff &b)
+{
+    float p, q, s, t;
+    ff_prod(a, b, p, q);
+    two_sum(A.s, p, s, t);
+    A.s = s;
+    A.lo = __fadd_rn(A.lo, __fadd_rn(q, t));
+}
+
+// A += c (a pair)
+__device__ __forceinline__ void acc_add(ffacc &A, const ff &c)
+{
+    float s, t;
+    two_sum(A.s, c.hi, s, t);
+    A.s = s;
+    A.lo = __fadd_rn(A.lo, __fadd_rn(c.lo, t));
+}
+
+// The accumulated sum as a normalised pair.
+__device__ __forceinline__ ff acc_result(const ffacc &A)
+{
+    ff r;
+    two_sum(A.s, A.lo, r.hi, r.lo);
+    return r;
+}
+
+// Exact scalings of a pair by powers of two and its negation (binary32 operations that are exact away
+// from the subnormal range, which the callers' range checks keep clear of).
+__device__ __forceinline__ ff ff_scale(const ff &a, float pow2) { return ff{a.hi * pow2, a.lo * pow2}; }
+__device__ __forceinline__ ff ff_neg(const ff &a) { return ff{-a.hi, -a.lo}; }
+
 // a - b for pairs, normalised.
 __device__ __forceinline__ ff sub_ff(const ff &a, const ff &b)
 {

@@ -38,14 +38,34 @@ def run_bwd(x, gout, dtype="f64"):
     return gin.cpu().numpy()
 
 
+@pytest.mark.parametrize("dtype", ["f64", "f64_ff"])
 @pytest.mark.parametrize("which", [("gamma", "dtg"), ("ginv", "gamma", "dbcov", "dtg"), ("dtg",), ("gamma",),
                                    ("dbcov",), ("ginv",), ("ginv", "dtg")])
-def test_adjoint_matches_oracle(which):
+def test_adjoint_matches_oracle(which, dtype):
     n = 4096
     x = gridgen.random_grid(n, 3)
     gout = upstream(n, 3, which)
-    assert_components(run_bwd(x, gout), oracle.backward(x, gout), TOL_F64, names=IN_NAMES,
-                      what="adjoint %s" % (which,))
+    assert_components(run_bwd(x, gout, dtype), oracle.backward(x, gout), TOL_F64, names=IN_NAMES,
+                      what="adjoint %s %s" % (dtype, which))
+
+
+def test_ff_adjoint_special_cases():
+    """Exact zeros (conformal grid with beta = K = 0), values outside the pair range (binary64 fallback
+    per point) and a partially absent upstream group, for the float-float adjoint."""
+    x = gridgen.conformal_grid(16)
+    n = x.shape[1]
+    gout = upstream(n, 4, ("ginv", "gamma", "dbcov", "dtg"))
+    assert_components(run_bwd(x, gout, "f64_ff"), oracle.backward(x, gout), TOL_F64, names=IN_NAMES, what="ff conformal")
+    n = 2048
+    x = gridgen.random_grid(n, 44)
+    x[31, 0:8] = 2.0 ** 70
+    x[6 + 4, 8:16] = -1e200
+    gout = upstream(n, 44, ("gamma", "dtg", "dbcov"))
+    gout[24 + 2] = None
+    y = run_bwd(x, gout, "f64_ff")
+    ref = oracle.backward(x, gout)
+    for lo, hi in [(0, 8), (8, 16), (16, n)]:
+        assert_components(y[:, lo:hi], ref[:, lo:hi], TOL_F64, names=IN_NAMES, what="ff rows %d-%d" % (lo, hi))
 
 
 def test_adjoint_partial_group_and_all_null():
@@ -59,11 +79,13 @@ def test_adjoint_partial_group_and_all_null():
     assert np.all(zero == 0.0)
 
 
+@pytest.mark.parametrize("dtype", ["f64", "f64_ff"])
 @pytest.mark.parametrize("n", [1, 127, 129, 65537])
-def test_adjoint_ragged(n):
+def test_adjoint_ragged(n, dtype):
     x = gridgen.random_grid(n, 50 + n)
     gout = upstream(n, 50 + n, ("ginv", "gamma", "dbcov", "dtg"))
-    assert_components(run_bwd(x, gout), oracle.backward(x, gout), TOL_F64, names=IN_NAMES, what="n=%d" % n)
+    assert_components(run_bwd(x, gout, dtype), oracle.backward(x, gout), TOL_F64, names=IN_NAMES,
+                      what="%s n=%d" % (dtype, n))
 
 
 def _loss_points(y, gout_d):
@@ -97,10 +119,13 @@ def test_full_size_adjoint_finite_differences():
         assert err <= 1e-7, (IN_NAMES[s], err)
     rng = np.random.default_rng(3)
     idx = np.unique(np.concatenate([np.arange(512), np.arange(n - 512, n), rng.integers(0, n, 15000)]))
-    gi = gin[:, torch.from_numpy(idx).to(dev())].cpu().numpy()
     ref = oracle.backward(np.ascontiguousarray(x[:, idx]), [None if g is None else np.ascontiguousarray(g[idx])
                                                             for g in gout])
+    gi = gin[:, torch.from_numpy(idx).to(dev())].cpu().numpy()
     assert_components(gi, ref, TOL_F64, names=IN_NAMES, what="N=2^22 sampled adjoint")
+    gin_ff = tl.tl_dtg_backward(xd, gd, dtype="f64_ff")
+    gi = gin_ff[:, torch.from_numpy(idx).to(dev())].cpu().numpy()
+    assert_components(gi, ref, TOL_F64, names=IN_NAMES, what="N=2^22 sampled float-float adjoint")
 
 
 def test_autograd_function_matches_oracle_and_torch_autograd():
