@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--only", default=None, choices=["forward", "adjoint", "batched"],
                     help="run just one form on --n points (or --grids subgrids) and print its timing; for profiling")
     ap.add_argument("--grids", type=int, default=600)
+    ap.add_argument("--suite", default=None, help="comma-separated grid sizes: run the Eqs. 9-21 expression suite")
     return ap.parse_args()
 
 
@@ -332,6 +333,14 @@ def extras(dev, stream, steps, x64, hbm):
                       "ms_600_launches": ms_sep, "ms_600_launches_in_graph": ms_sepg}
     plan.close()
     del xs, ys
+    # the expression suite of Sec. 5.1 at a realistic multi-domain grid size and at a large one
+    rows = suite(dev, stream, [32768, 1 << 22], reps=max(3, steps // 2))
+    out["expression_suite"] = {
+        "workload": "Eqs. 9-21, binary64, N(0,1) components; BW_eff = 8 B x N_e x N / t (Eq. 8)",
+        "rows": [{"eq": r["eq"], "n": r["n"], "fused_GB_s": round(r["fused_GB_s"], 1),
+                  "arrays_GB_s": round(r["arrays_GB_s"], 1), "fused_graph_GB_s": round(r["fused_graph_GB_s"], 1),
+                  "arrays_graph_GB_s": round(r["arrays_graph_GB_s"], 1), "arrays_launches": r["arrays_launches"]}
+                 for r in rows]}
     return out
 
 
@@ -376,8 +385,67 @@ def only_form(args):
                       "points_per_s": units / ms * 1e3}), flush=True)
 
 
+EXPR_NAMES = {9: "A_i=B_i", 10: "A_ij=B_ij", 11: "A_ijk=B_ijk", 12: "A_i=B_i+C_i", 13: "A_i=B_i+C_i+D_i",
+              14: "A_i=B_i+C_i+D_i+E_i", 15: "A_ij=B_iC_j", 16: "A_ijk=B_iC_jD_k", 17: "A_ijkl=B_iC_jD_kE_l",
+              18: "A_ijkl=B_i^mE_mjkl", 19: "A_ijkl=C_j^nB_i^mE_mnkl", 20: "A_ijkl=D_k^oC_j^nB_i^mE_mnol",
+              21: "K_ij=2alpha g_ij+beta_i beta_j"}
+
+
+def suite(dev, stream, sizes, reps=10):
+    """Effective bandwidth (Eq. 8, N_d = 0) of the benchmark expressions of Sec. 5.1, fused ("Tensors")
+    and one launch per component / contracted index ("Arrays"), at each grid size.  Each evaluation is
+    one direct call of the C entry point with prebuilt pointer tables (`*_ms`: host launches included),
+    and the same evaluation captured once in a CUDA graph and replayed (`*_graph_ms`)."""
+    import ctypes
+    import torch
+    import gridgen
+    import paper_1804_10120_gb300 as tl
+    L = tl.lib()
+    L.tl_expr_eval.argtypes = [ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int,
+                               ctypes.c_void_p]
+    L.tl_expr_eval.restype = ctypes.c_int
+    side = torch.cuda.Stream(dev)
+    rows = []
+    for eq in range(9, 22):
+        n_in, n_out = tl.tl_expr_arity(eq)
+        for n in sizes:
+            x = torch.from_numpy(gridgen.normal_fields(n_in, n, eq, 5000)).to(dev)
+            y = torch.empty((n_out, n), dtype=torch.float64, device=dev)
+            tin = (ctypes.c_void_p * n_in)(*[x[q].data_ptr() for q in range(n_in)])
+            tout = (ctypes.c_void_p * n_out)(*[y[q].data_ptr() for q in range(n_out)])
+            row = {"eq": eq, "expr": EXPR_NAMES[eq], "n": n, "N_e": n_in + n_out}
+            for mode, code in (("fused", 0), ("arrays", 1)):
+                h = ctypes.c_void_p(stream.cuda_stream)
+                launches = 1 if code == 0 else n_out * (3 ** (eq - 17) if eq in (18, 19, 20) else 1)
+                r = reps if launches < 300 else max(2, reps // 4)
+
+                def call(hs=h):
+                    assert L.tl_expr_eval(eq, ctypes.byref(tin), ctypes.byref(tout), n, code, hs) == 0
+                ms = cuda_time(call, r, stream, warmup=2)
+                side.wait_stream(stream)
+                g = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(g, stream=side):
+                    call(ctypes.c_void_p(side.cuda_stream))
+                gms = cuda_time(g.replay, r, torch.cuda.current_stream(dev), warmup=2)
+                del g
+                row.update({mode + "_launches": launches, mode + "_ms": ms, mode + "_GB_s": 8 * (n_in + n_out) * n / ms / 1e6,
+                            mode + "_graph_ms": gms, mode + "_graph_GB_s": 8 * (n_in + n_out) * n / gms / 1e6})
+            rows.append(row)
+            del x, y
+    return rows
+
+
 def main():
     args = parse()
+    if args.suite:
+        import torch
+        from paper_1804_10120_gb300 import build as tlbuild
+        tlbuild.build()
+        dev = torch.device("cuda", 0)
+        torch.cuda.set_device(dev)
+        for row in suite(dev, torch.cuda.current_stream(dev), [int(v) for v in args.suite.split(",")], args.steps):
+            print(json.dumps(row), flush=True)
+        return
     if args.impl == "reference":
         return reference_arm(args)
     if args.only:

@@ -168,6 +168,23 @@ TL_API void tl_batch_plan_destroy(tl_batch_plan *plan);
 TL_API tl_status tl_dtg_batched_noalloc(const tl_dtg_in *in, const tl_dtg_out *out, const int64_t *n, int32_t G,
                                         tl_dtype dtype, tl_stream stream);
 
+/*
+ * The benchmark expressions of Sec. 5.1, Eqs. 9-21 (assignments, additions, outer products,
+ * contractions, and K_ij = 2 alpha g_ij + beta_i beta_j), binary64, every index spatial.  Components are
+ * arrays of n doubles, row-major over the indices as written (B_i^m -> B[3i+m], E_mjkl ->
+ * E[27m+9j+3k+l]); Eq. 21's g_ij and K_ij are packed symmetric.  `in` lists the operands in the order
+ * they appear in the equation as printed (Eq. 19: B, C, E; Eq. 20: B, C, D, E; Eq. 21: alpha, g,
+ * beta), `out` the left-hand side; tl_expr_arity gives both counts.
+ *   TL_EXPR_FUSED   one kernel for the whole expression (the paper's "Tensors")
+ *   TL_EXPR_ARRAYS  explicit loops over left-hand-side components and contracted index values around
+ *                   pointwise kernels, one launch each (the paper's "Arrays", Sec. 5.5)
+ * Same argument rules as tl_dtg_forward (device arrays, element alignment, no aliasing of outputs).
+ */
+typedef enum { TL_EXPR_FUSED = 0, TL_EXPR_ARRAYS = 1 } tl_expr_mode;
+TL_API tl_status tl_expr_arity(int32_t eq, int32_t *n_in, int32_t *n_out);
+TL_API tl_status tl_expr_eval(int32_t eq, const double *const *in, double *const *out, int64_t n, tl_expr_mode mode,
+                              tl_stream stream);
+
 TL_API const char *tl_status_string(tl_status s);
 TL_API const char *tl_last_error(void);
 /* Library version as MAJOR*10000 + MINOR*100 + PATCH. */

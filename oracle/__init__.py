@@ -24,6 +24,7 @@ N_IN = 43
 N_OUT = 39
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "dtg_oracle.c")
+_SRC_EXPR = os.path.join(_HERE, "expr_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -31,11 +32,12 @@ _lib = None
 
 def build(force=False):
     """Compile liboracle.so with gcc (plain C99, -O2, no FP contraction)."""
-    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= max(os.path.getmtime(_SRC),
+                                                                            os.path.getmtime(_SRC_EXPR)):
         return _LIB
     tmp = _LIB + ".tmp%d" % os.getpid()
     subprocess.check_call(["gcc", "-std=c99", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
-                           "-shared", "-o", tmp, _SRC, "-lm"])
+                           "-shared", "-o", tmp, _SRC, _SRC_EXPR, "-lm"])
     os.replace(tmp, _LIB)
     return _LIB
 
@@ -51,6 +53,8 @@ def lib():
             L.oracle_dtg_backward.argtypes = [ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P),
                                               ctypes.c_int64]
             L.oracle_metric_det.argtypes = [ctypes.POINTER(P), P, ctypes.c_int64]
+            L.oracle_expr.argtypes = [ctypes.c_int, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.c_int64]
+            L.oracle_expr.restype = ctypes.c_int
             for f in (L.oracle_dtg_forward, L.oracle_dtg_backward, L.oracle_metric_det):
                 f.restype = ctypes.c_int
             _lib = L
@@ -141,4 +145,22 @@ def forward_threaded(inputs, out, threads):
         th.start()
     for th in ths:
         th.join()
+    return out
+
+
+# Benchmark expressions of Sec. 5.1: (number of input arrays, number of output arrays) per equation.
+EXPR_ARITY = {9: (3, 3), 10: (9, 9), 11: (27, 27), 12: (6, 3), 13: (9, 3), 14: (12, 3), 15: (6, 9),
+              16: (9, 27), 17: (12, 81), 18: (90, 81), 19: (99, 81), 20: (108, 81), 21: (10, 6)}
+
+
+def expr(eq, inputs):
+    """Evaluate benchmark expression `eq` (9..21) literally; inputs [n_in, n] -> outputs [n_out, n]."""
+    n_in, n_out = EXPR_ARITY[eq]
+    rows = _rows(inputs, n_in)
+    n = rows[0].shape[0]
+    out = np.empty((n_out, n), dtype=np.float64)
+    orows = [out[s] for s in range(n_out)]
+    rc = lib().oracle_expr(eq, _table(rows, n_in, n), _table(orows, n_out, n), n)
+    if rc != 0:
+        raise ValueError("oracle_expr rejected its arguments")
     return out

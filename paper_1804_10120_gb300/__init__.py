@@ -373,3 +373,46 @@ def tl_dtg_batched(plan, stream=None):
 
 def tl_dtg_batched_tune(plan, stream=None):
     return plan.tune(stream)
+
+
+# ----------------------------------------------------------------------------- benchmark expressions
+
+TL_EXPR_FUSED, TL_EXPR_ARRAYS = 0, 1
+EXPR_MODES = {"fused": TL_EXPR_FUSED, "tensors": TL_EXPR_FUSED, "arrays": TL_EXPR_ARRAYS}
+
+
+def tl_expr_arity(eq):
+    L = lib()
+    L.tl_expr_arity.argtypes = [ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
+    L.tl_expr_arity.restype = ctypes.c_int
+    a, b = ctypes.c_int32(), ctypes.c_int32()
+    _check(L.tl_expr_arity(eq, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+def tl_expr_eval(eq, inputs, outputs=None, mode="fused", stream=None):
+    """Benchmark expression `eq` (Eqs. 9-21 of Sec. 5.1) on device float64 tensors: inputs [n_in, n] (or
+    n_in arrays), outputs [n_out, n] (allocated if not given); mode "fused" (one kernel) or "arrays"
+    (one launch per component and contracted index)."""
+    import torch
+    import torch as _t
+    n_in, n_out = tl_expr_arity(eq)
+    rows = _rows(inputs, n_in, "inputs")
+    n = rows[0].shape[0]
+    dev = rows[0].device
+    if outputs is None:
+        outputs = _t.empty((n_out, n), dtype=_t.float64, device=dev)
+    orows = _rows(outputs, n_out, "outputs")
+    itab = _table(rows, n_in, n, _t.float64, "cuda", "inputs")
+    otab = _table(orows, n_out, n, _t.float64, "cuda", "outputs")
+    if n == 0:
+        _nonnull_empty(itab, n_in)
+        _nonnull_empty(otab, n_out)
+    L = lib()
+    L.tl_expr_eval.argtypes = [ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int,
+                               ctypes.c_void_p]
+    L.tl_expr_eval.restype = ctypes.c_int
+    with torch.cuda.device(dev):
+        _check(L.tl_expr_eval(eq, ctypes.byref(itab), ctypes.byref(otab), n, EXPR_MODES[mode],
+                              _stream_handle(stream, dev)))
+    return outputs
