@@ -333,6 +333,17 @@ def extras(dev, stream, steps, x64, hbm):
                       "ms_600_launches": ms_sep, "ms_600_launches_in_graph": ms_sepg}
     plan.close()
     del xs, ys
+    # the same chain written as a tensor-index program, emitted and compiled at run time
+    from tests.jit_programs import PROGRAMS
+    k = tl.JitKernel(PROGRAMS["chain"])
+    y = torch.empty((39, n), dtype=torch.float64, device=dev)
+    ms_gen = cuda_time(lambda: k.launch(x64, y, stream=stream), steps, stream)
+    out["generated_chain"] = {"workload": "single grid N=2^24, seed 1; the chain as a 16-statement index program "
+                                          "compiled by the runtime generator (NVRTC, sm_103a)",
+                              "ms": ms_gen, "points_per_s": n / ms_gen * 1e3, "GB_s": 656 * n / ms_gen / 1e6,
+                              "hbm_frac": 656 * n / ms_gen / 1e6 / hbm}
+    k.close()
+    del y
     # the expression suite of Sec. 5.1 at a realistic multi-domain grid size and at a large one
     rows = suite(dev, stream, [32768, 1 << 22], reps=max(3, steps // 2))
     out["expression_suite"] = {

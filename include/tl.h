@@ -185,6 +185,31 @@ TL_API tl_status tl_expr_arity(int32_t eq, int32_t *n_in, int32_t *n_out);
 TL_API tl_status tl_expr_eval(int32_t eq, const double *const *in, double *const *out, int64_t n, tl_expr_mode mode,
                               tl_stream stream);
 
+/*
+ * Runtime generator (the GB300 counterpart of the paper's CodeWriter, Secs. 3-4): a program of tensor
+ * index statements is parsed, checked against the paper's index rules, emitted as CUDA source for ONE
+ * kernel with one thread per grid point, and compiled by NVRTC for sm_103a (libnvrtc is loaded at
+ * first use).  Language, one item per ';':
+ *   in NAME(d0, d1, ...) sym(a,b) ...;   out NAME(...);   temp NAME(...);   in NAME;  (scalar)
+ *   index l(d) ...;  (a letter's range when it differs from its slot's dimension)
+ *   NAME(idx, ...) = EXPR;   idx: letter, letter+k, letter-k, integer;  EXPR: numbers, NAME(idx...),
+ *   + - * / (division by scalars only), unary -, parentheses, Sum(letter, EXPR)
+ * `temp` tensors live in registers; only `out` tensors are stored.  Each stored component a left-hand
+ * side reaches is evaluated once (a symmetric pair is one element).  The component tables list, for every `in` (then every
+ * `out`) tensor in declaration order, its stored index tuples (symmetric pairs ascending) in row-major
+ * order; tl_jit_info returns the counts, the generated source and one "in|out NAME i j ..." line per
+ * table entry.  tl_jit_compile runs on the host without a device (TL_ERR_INVALID_ARG with the
+ * parser's or NVRTC's message in `log` on failure); tl_jit_launch loads the module on the current
+ * device at its first launch there (not capturable), then enqueues one launch on `stream`.
+ */
+typedef struct tl_jit_kernel tl_jit_kernel;
+TL_API tl_status tl_jit_compile(const char *program, tl_jit_kernel **kernel, char *log, size_t log_size);
+TL_API tl_status tl_jit_info(const tl_jit_kernel *kernel, int32_t *n_in, int32_t *n_out, const char **source,
+                             const char **component_names);
+TL_API tl_status tl_jit_launch(tl_jit_kernel *kernel, const double *const *in, double *const *out, int64_t n,
+                               tl_stream stream);
+TL_API void tl_jit_destroy(tl_jit_kernel *kernel);
+
 TL_API const char *tl_status_string(tl_status s);
 TL_API const char *tl_last_error(void);
 /* Library version as MAJOR*10000 + MINOR*100 + PATCH. */

@@ -416,3 +416,71 @@ def tl_expr_eval(eq, inputs, outputs=None, mode="fused", stream=None):
         _check(L.tl_expr_eval(eq, ctypes.byref(itab), ctypes.byref(otab), n, EXPR_MODES[mode],
                               _stream_handle(stream, dev)))
     return outputs
+
+
+# --------------------------------------------------------------------------------- runtime generator
+
+class JitKernel:
+    """A tensor-index program compiled by tl_jit_compile (parse, index checks, CUDA source, NVRTC).
+    `inputs` / `outputs` list the component tables as (tensor name, index tuple); `source` is the
+    generated CUDA."""
+
+    def __init__(self, program):
+        L = lib()
+        vp = ctypes.c_void_p
+        L.tl_jit_compile.argtypes = [ctypes.c_char_p, ctypes.POINTER(vp), ctypes.c_char_p, ctypes.c_size_t]
+        L.tl_jit_compile.restype = ctypes.c_int
+        L.tl_jit_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                  ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_char_p)]
+        L.tl_jit_info.restype = ctypes.c_int
+        L.tl_jit_launch.argtypes = [vp, vp, vp, ctypes.c_int64, vp]
+        L.tl_jit_launch.restype = ctypes.c_int
+        L.tl_jit_destroy.argtypes = [vp]
+        L.tl_jit_destroy.restype = None
+        h = vp()
+        log = ctypes.create_string_buffer(4096)
+        rc = L.tl_jit_compile(program.encode(), ctypes.byref(h), log, len(log))
+        if rc != 0:
+            raise TLError(rc, log.value.decode())
+        self._h = h
+        ni, no = ctypes.c_int32(), ctypes.c_int32()
+        src, names = ctypes.c_char_p(), ctypes.c_char_p()
+        _check(L.tl_jit_info(h, ctypes.byref(ni), ctypes.byref(no), ctypes.byref(src), ctypes.byref(names)))
+        self.n_in, self.n_out = ni.value, no.value
+        self.source = src.value.decode()
+        self.inputs, self.outputs = [], []
+        for line in names.value.decode().splitlines():
+            kind, name, *idx = line.split()
+            (self.inputs if kind == "in" else self.outputs).append((name, tuple(int(v) for v in idx)))
+
+    def launch(self, inputs, outputs=None, stream=None):
+        import torch
+        rows = _rows(inputs, self.n_in, "inputs") if self.n_in else []
+        n = rows[0].shape[0] if rows else (outputs.shape[1] if outputs is not None else 0)
+        dev = rows[0].device if rows else torch.device("cuda", torch.cuda.current_device())
+        if outputs is None:
+            outputs = torch.empty((self.n_out, n), dtype=torch.float64, device=dev)
+        orows = _rows(outputs, self.n_out, "outputs")
+        itab = _table(rows, self.n_in, n, torch.float64, "cuda", "inputs") if self.n_in else (ctypes.c_void_p * 1)()
+        otab = _table(orows, self.n_out, n, torch.float64, "cuda", "outputs")
+        if n == 0:
+            _nonnull_empty(itab, max(self.n_in, 1))
+            _nonnull_empty(otab, self.n_out)
+        with torch.cuda.device(dev):
+            _check(lib().tl_jit_launch(self._h, ctypes.byref(itab), ctypes.byref(otab), n, _stream_handle(stream, dev)))
+        return outputs
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().tl_jit_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def tl_jit_compile(program):
+    return JitKernel(program)

@@ -1,0 +1,1013 @@
+// jit.cu -- runtime generator: a tensor-index program -> CUDA source -> NVRTC -> one fused sm_103a kernel.
+//
+// The GB300 counterpart of the paper's CodeWriter (Secs. 3-4): instead of registering every expression
+// template at link time and emitting one kernel per expression with one thread per (point, component),
+// a whole program of index statements is parsed at run time and emitted as ONE kernel with one thread
+// per grid point that evaluates every component of every statement, keeping intermediates (`temp`
+// tensors) in registers and storing only the `out` tensors.
+//
+// Language (one declaration or statement per ';'):
+//   in  NAME(d0, d1, ...) [sym(a,b) ...];   input tensor, slot dimensions (3 or 4), symmetric slot pairs
+//   out NAME(...) [sym(...)];                output tensor        temp NAME(...) [sym(...)];  register-only
+//   in  NAME;                                scalar (rank 0)
+//   index l(d), m(d) ...;                    explicit ranges of index letters (default: the slot dimension)
+//   NAME(idx, ...) = EXPR;                   statement; idx: letter, letter+k / letter-k (offset), integer
+//   EXPR: numbers, NAME(idx...), + - * /, unary -, ( ), Sum(letter, EXPR)
+// Index rules (the paper's, Sec. 2.3): both operands of + and - carry the same free indices; a letter
+// may not appear in both factors of a product (contractions are written with Sum); the right-hand
+// side's free indices equal the left-hand side's letters.  A letter ranges over its slot's dimension
+// unless declared with `index l(d);` (the paper's spatial i_ on a spacetime slot).  Each stored
+// component the left-hand side reaches is evaluated once, at the first index assignment (row-major)
+// that reaches it -- a symmetric pair is stored once, as in the paper's lookup table.
+// Component storage order of a tensor: its stored index tuples in row-major order.
+#include <dlfcn.h>
+
+#include <functional>
+
+#include <algorithm>
+#include <cctype>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <set>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "tl_host.h"
+
+namespace tl {
+namespace jit {
+
+// ---------------------------------------------------------------------------------------------- model
+struct Tensor {
+    std::string name;
+    int kind = 0;                               // 0 in, 1 out, 2 temp
+    std::vector<int> dims;
+    std::vector<std::pair<int, int>> sym;       // symmetric slot pairs
+    std::vector<std::vector<int>> stored;       // stored index tuples, storage order
+    std::map<std::vector<int>, int> slot_of;    // any index tuple -> storage position
+    int table_base = 0;                         // first position in the in/out table
+};
+
+struct Idx {
+    bool fixed = false;
+    int value = 0;      // fixed value, or offset
+    char letter = 0;
+};
+
+struct Expr {
+    enum Kind { NUM, REF, NEG, ADD, SUB, MUL, DIV, SUM } kind;
+    double num = 0;
+    int tensor = -1;
+    std::vector<Idx> idx;
+    char sum_letter = 0;
+    std::unique_ptr<Expr> a, b;
+};
+
+struct Stmt {
+    int tensor;
+    std::vector<Idx> lhs;
+    std::unique_ptr<Expr> rhs;
+};
+
+struct Program {
+    std::map<char, int> ranges;                 // declared index ranges ("index i(3);")
+    std::vector<Tensor> tensors;
+    std::vector<Stmt> stmts;
+    int n_in = 0, n_out = 0;
+    std::string source, names;
+};
+
+struct Error {
+    std::string msg;
+};
+
+// ----------------------------------------------------------------------------------------------- lexer
+struct Lexer {
+    const std::string &s;
+    size_t p = 0;
+    explicit Lexer(const std::string &src) : s(src) {}
+    void ws()
+    {
+        while (p < s.size()) {
+            if (isspace((unsigned char)s[p]))
+                ++p;
+            else if (s[p] == '#' || (s[p] == '/' && p + 1 < s.size() && s[p + 1] == '/'))
+                while (p < s.size() && s[p] != '\n')
+                    ++p;
+            else
+                break;
+        }
+    }
+    bool eof()
+    {
+        ws();
+        return p >= s.size();
+    }
+    char peek()
+    {
+        ws();
+        return p < s.size() ? s[p] : '\0';
+    }
+    bool accept(char c)
+    {
+        if (peek() == c) {
+            ++p;
+            return true;
+        }
+        return false;
+    }
+    void expect(char c)
+    {
+        if (!accept(c))
+            throw Error{std::string("expected '") + c + "' at offset " + std::to_string(p)};
+    }
+    std::string ident()
+    {
+        ws();
+        size_t b = p;
+        if (p < s.size() && (isalpha((unsigned char)s[p]) || s[p] == '_'))
+            while (p < s.size() && (isalnum((unsigned char)s[p]) || s[p] == '_'))
+                ++p;
+        if (b == p)
+            throw Error{"expected a name at offset " + std::to_string(p)};
+        return s.substr(b, p - b);
+    }
+    bool at_number()
+    {
+        char c = peek();
+        return isdigit((unsigned char)c) || c == '.';
+    }
+    double number()
+    {
+        ws();
+        const char *b = s.c_str() + p;
+        char *e = nullptr;
+        double v = strtod(b, &e);
+        if (e == b)
+            throw Error{"expected a number at offset " + std::to_string(p)};
+        p += (size_t)(e - b);
+        return v;
+    }
+    int integer()
+    {
+        ws();
+        size_t b = p;
+        while (p < s.size() && isdigit((unsigned char)s[p]))
+            ++p;
+        if (b == p)
+            throw Error{"expected an integer at offset " + std::to_string(p)};
+        return atoi(s.substr(b, p - b).c_str());
+    }
+};
+
+// ---------------------------------------------------------------------------------------------- parser
+struct Parser {
+    Lexer L;
+    Program &P;
+    std::map<std::string, int> by_name;
+    Parser(const std::string &src, Program &prog) : L(src), P(prog) {}
+
+    int tensor_id(const std::string &n)
+    {
+        auto it = by_name.find(n);
+        if (it == by_name.end())
+            throw Error{"unknown tensor '" + n + "'"};
+        return it->second;
+    }
+
+    std::vector<Idx> index_list()
+    {
+        std::vector<Idx> v;
+        if (!L.accept('('))
+            return v;
+        if (L.accept(')'))
+            return v;
+        do {
+            Idx i;
+            if (L.at_number()) {
+                i.fixed = true;
+                i.value = L.integer();
+            } else {
+                std::string id = L.ident();
+                if (id.size() != 1 || !islower((unsigned char)id[0]))
+                    throw Error{"index names are single lower-case letters (got '" + id + "')"};
+                i.letter = id[0];
+                if (L.accept('+'))
+                    i.value = L.integer();
+                else if (L.accept('-'))
+                    i.value = -L.integer();
+            }
+            v.push_back(i);
+        } while (L.accept(','));
+        L.expect(')');
+        return v;
+    }
+
+    void declaration(int kind)
+    {
+        Tensor t;
+        t.kind = kind;
+        t.name = L.ident();
+        if (by_name.count(t.name))
+            throw Error{"tensor '" + t.name + "' declared twice"};
+        if (L.accept('(')) {
+            if (!L.accept(')')) {
+                do {
+                    int d = L.integer();
+                    if (d < 1 || d > 4)
+                        throw Error{"slot dimension of '" + t.name + "' must be 1..4"};
+                    t.dims.push_back(d);
+                } while (L.accept(','));
+                L.expect(')');
+            }
+        }
+        while (!L.eof() && L.peek() != ';') {
+            std::string kw = L.ident();
+            if (kw != "sym")
+                throw Error{"unexpected '" + kw + "' in the declaration of '" + t.name + "'"};
+            L.expect('(');
+            int a = L.integer();
+            L.expect(',');
+            int b = L.integer();
+            L.expect(')');
+            if (a == b || a < 0 || b < 0 || a >= (int)t.dims.size() || b >= (int)t.dims.size() || t.dims[a] != t.dims[b])
+                throw Error{"bad sym(" + std::to_string(a) + "," + std::to_string(b) + ") for '" + t.name + "'"};
+            t.sym.push_back({std::min(a, b), std::max(a, b)});
+        }
+        // stored components: canonical tuples (each symmetric pair ascending), row-major order
+        const int rank = (int)t.dims.size();
+        std::vector<int> tup(rank, 0);
+        for (;;) {
+            std::vector<int> canon = tup;
+            bool changed = true;   // bubble through the pairs until every pair is ascending
+            while (changed) {
+                changed = false;
+                for (auto &pr : t.sym)
+                    if (canon[pr.first] > canon[pr.second]) {
+                        std::swap(canon[pr.first], canon[pr.second]);
+                        changed = true;
+                    }
+            }
+            if (canon == tup) {
+                t.slot_of[tup] = (int)t.stored.size();
+                t.stored.push_back(tup);
+            }
+            int r = rank - 1;
+            while (r >= 0 && ++tup[r] == t.dims[r])
+                tup[r--] = 0;
+            if (r < 0)
+                break;
+        }
+        // every tuple maps to its canonical tuple's slot
+        std::vector<int> all(rank, 0);
+        for (;;) {
+            std::vector<int> canon = all;
+            bool changed = true;
+            while (changed) {
+                changed = false;
+                for (auto &pr : t.sym)
+                    if (canon[pr.first] > canon[pr.second]) {
+                        std::swap(canon[pr.first], canon[pr.second]);
+                        changed = true;
+                    }
+            }
+            t.slot_of[all] = t.slot_of.at(canon);
+            int r = rank - 1;
+            while (r >= 0 && ++all[r] == t.dims[r])
+                all[r--] = 0;
+            if (r < 0)
+                break;
+        }
+        by_name[t.name] = (int)P.tensors.size();
+        P.tensors.push_back(std::move(t));
+    }
+
+    std::unique_ptr<Expr> primary()
+    {
+        auto e = std::make_unique<Expr>();
+        if (L.accept('(')) {
+            auto inner = sum_expr();
+            L.expect(')');
+            return inner;
+        }
+        if (L.accept('-')) {
+            e->kind = Expr::NEG;
+            e->a = primary();
+            return e;
+        }
+        if (L.at_number()) {
+            e->kind = Expr::NUM;
+            e->num = L.number();
+            return e;
+        }
+        std::string id = L.ident();
+        if (id == "Sum") {
+            L.expect('(');
+            std::string l = L.ident();
+            if (l.size() != 1 || !islower((unsigned char)l[0]))
+                throw Error{"Sum needs a single-letter index"};
+            L.expect(',');
+            e->kind = Expr::SUM;
+            e->sum_letter = l[0];
+            e->a = sum_expr();
+            L.expect(')');
+            return e;
+        }
+        e->kind = Expr::REF;
+        e->tensor = tensor_id(id);
+        e->idx = index_list();
+        if (e->idx.size() != P.tensors[e->tensor].dims.size())
+            throw Error{"'" + id + "' has rank " + std::to_string(P.tensors[e->tensor].dims.size())};
+        return e;
+    }
+
+    std::unique_ptr<Expr> product()
+    {
+        auto e = primary();
+        for (;;) {
+            Expr::Kind k;
+            if (L.accept('*'))
+                k = Expr::MUL;
+            else if (L.accept('/'))
+                k = Expr::DIV;
+            else
+                return e;
+            auto n = std::make_unique<Expr>();
+            n->kind = k;
+            n->a = std::move(e);
+            n->b = primary();
+            e = std::move(n);
+        }
+    }
+
+    std::unique_ptr<Expr> sum_expr()
+    {
+        auto e = product();
+        for (;;) {
+            Expr::Kind k;
+            if (L.accept('+'))
+                k = Expr::ADD;
+            else if (L.accept('-'))
+                k = Expr::SUB;
+            else
+                return e;
+            auto n = std::make_unique<Expr>();
+            n->kind = k;
+            n->a = std::move(e);
+            n->b = product();
+            e = std::move(n);
+        }
+    }
+
+    void parse()
+    {
+        while (!L.eof()) {
+            size_t save = L.p;
+            std::string id = L.ident();
+            if (id == "index") {
+                do {
+                    std::string l = L.ident();
+                    if (l.size() != 1 || !islower((unsigned char)l[0]))
+                        throw Error{"index names are single lower-case letters (got '" + l + "')"};
+                    L.expect('(');
+                    const int d = L.integer();
+                    L.expect(')');
+                    if (d < 1 || d > 4)
+                        throw Error{"index range must be 1..4"};
+                    P.ranges[l[0]] = d;
+                } while (L.accept(','));
+                L.expect(';');
+                continue;
+            }
+            if (id == "in" || id == "out" || id == "temp") {
+                // "in NAME..." is a declaration unless "in" is itself followed by '(' or '='
+                char c = L.peek();
+                if (c != '(' && c != '=') {
+                    declaration(id == "in" ? 0 : id == "out" ? 1 : 2);
+                    L.expect(';');
+                    continue;
+                }
+            }
+            L.p = save;
+            Stmt st;
+            st.tensor = tensor_id(L.ident());
+            if (P.tensors[st.tensor].kind == 0)
+                throw Error{"cannot assign to input '" + P.tensors[st.tensor].name + "'"};
+            st.lhs = index_list();
+            if (st.lhs.size() != P.tensors[st.tensor].dims.size())
+                throw Error{"left-hand side '" + P.tensors[st.tensor].name + "' has the wrong rank"};
+            L.expect('=');
+            st.rhs = sum_expr();
+            L.expect(';');
+            P.stmts.push_back(std::move(st));
+        }
+    }
+};
+
+// ------------------------------------------------------------------------------- index checks, codegen
+using Binding = std::map<char, int>;
+
+// Free letters of an expression and the slot dimension each is used with; throws on rule violations.
+// `summed` holds the letters bound by enclosing Sums: only those may repeat (within one tensor or across
+// the two factors of a product), since the Sum is what contracts them.
+int range_of(const Program &P, char letter, int slot_dim)
+{
+    auto it = P.ranges.find(letter);
+    return it != P.ranges.end() ? it->second : slot_dim;
+}
+
+void free_letters(const Program &P, const Expr &e, std::map<char, int> &out, const std::set<char> &summed)
+{
+    auto merge = [&](const std::map<char, int> &f, const std::map<char, int> &g, bool product) {
+        for (auto &kv : g) {
+            auto it = f.find(kv.first);
+            if (it != f.end()) {
+                if (product && !summed.count(kv.first))
+                    throw Error{std::string("index '") + kv.first + "' appears in both factors of a product (use Sum)"};
+            }
+        }
+    };
+    switch (e.kind) {
+    case Expr::NUM:
+        return;
+    case Expr::REF: {
+        const Tensor &t = P.tensors[e.tensor];
+        for (size_t s = 0; s < e.idx.size(); ++s)
+            if (!e.idx[s].fixed) {
+                // a free letter takes its range from the left-hand side (or its declaration); uses on
+                // slots of other dimensions are bounds-checked when the code is generated
+                const int d = range_of(P, e.idx[s].letter, t.dims[s]);
+                auto it = out.find(e.idx[s].letter);
+                if (it != out.end() && !summed.count(e.idx[s].letter))
+                    throw Error{std::string("index '") + e.idx[s].letter + "' repeated within '" + t.name +
+                                "' (write contractions with Sum)"};
+                out[e.idx[s].letter] = d;
+            }
+        return;
+    }
+    case Expr::NEG:
+        free_letters(P, *e.a, out, summed);
+        return;
+    case Expr::ADD:
+    case Expr::SUB: {
+        std::map<char, int> fa, fb;
+        free_letters(P, *e.a, fa, summed);
+        free_letters(P, *e.b, fb, summed);
+        std::set<char> sa, sb;
+        for (auto &kv : fa)
+            sa.insert(kv.first);
+        for (auto &kv : fb)
+            sb.insert(kv.first);
+        if (sa != sb)
+            throw Error{"the operands of + / - carry different free indices"};
+        out.insert(fa.begin(), fa.end());
+        return;
+    }
+    case Expr::MUL:
+    case Expr::DIV: {
+        std::map<char, int> fa, fb;
+        free_letters(P, *e.a, fa, summed);
+        free_letters(P, *e.b, fb, summed);
+        if (e.kind == Expr::DIV && !fb.empty())
+            throw Error{"only scalar expressions may divide"};
+        merge(fa, fb, true);
+        out.insert(fa.begin(), fa.end());
+        out.insert(fb.begin(), fb.end());
+        return;
+    }
+    case Expr::SUM: {
+        if (summed.count(e.sum_letter))
+            throw Error{std::string("nested Sums over the same index '") + e.sum_letter + "'"};
+        std::set<char> inner = summed;
+        inner.insert(e.sum_letter);
+        std::map<char, int> fa;
+        free_letters(P, *e.a, fa, inner);
+        if (!fa.count(e.sum_letter))
+            throw Error{std::string("Sum over '") + e.sum_letter + "', which is not free in its operand"};
+        fa.erase(e.sum_letter);
+        merge(out, fa, false);
+        out.insert(fa.begin(), fa.end());
+        return;
+    }
+    }
+}
+
+// The range of a summation letter inside e: its declaration, or the common dimension of the slots it
+// indexes (an error when they differ and no declaration settles it).
+int letter_dim(const Program &P, const Expr &e, char l)
+{
+    std::set<int> dims;
+    std::function<void(const Expr &)> walk = [&](const Expr &x) {
+        if (x.kind == Expr::REF) {
+            for (size_t s = 0; s < x.idx.size(); ++s)
+                if (!x.idx[s].fixed && x.idx[s].letter == l)
+                    dims.insert(range_of(P, l, P.tensors[x.tensor].dims[s]));
+        }
+        if (x.a)
+            walk(*x.a);
+        if (x.b)
+            walk(*x.b);
+    };
+    walk(e);
+    if (dims.size() != 1)
+        throw Error{std::string("summation index '") + l + "' indexes slots of different dimensions: declare its range"};
+    return *dims.begin();
+}
+
+std::string value_name(const Program &P, int tensor, int slot)
+{
+    const Tensor &t = P.tensors[tensor];
+    return (t.kind == 0 ? "in_" : "v_") + t.name + "_" + std::to_string(slot);
+}
+
+std::string fmt_num(double v)
+{
+    char b[64];
+    snprintf(b, sizeof b, "%.17g", v);
+    std::string s(b);
+    if (s.find_first_of(".eEn") == std::string::npos)
+        s += ".0";
+    return "(" + s + ")";
+}
+
+// Code generation state for one kernel: inputs read, components defined so far, hoisted reciprocals.
+struct GenState {
+    std::set<int> used_inputs;
+    std::vector<std::set<int>> defined;
+    std::map<std::string, std::string> recip;   // divisor code -> variable holding its reciprocal
+    std::ostringstream *body = nullptr;
+};
+
+std::string gen(const Program &P, const Expr &e, Binding &bind, GenState &G);
+
+// The addends of a chain of + / - / unary -, each with its sign, generated for the current binding.
+void addends(const Program &P, const Expr &e, Binding &bind, GenState &G, int sign,
+             std::vector<std::pair<int, std::string>> &out)
+{
+    if (e.kind == Expr::ADD || e.kind == Expr::SUB) {
+        addends(P, *e.a, bind, G, sign, out);
+        addends(P, *e.b, bind, G, e.kind == Expr::ADD ? sign : -sign, out);
+    } else if (e.kind == Expr::NEG) {
+        addends(P, *e.a, bind, G, -sign, out);
+    } else if (e.kind == Expr::SUM) {
+        // a Sum of addends is itself a chain of additions
+        const int d = letter_dim(P, *e.a, e.sum_letter);
+        const bool shadow = bind.count(e.sum_letter) != 0;
+        const int saved = shadow ? bind[e.sum_letter] : 0;
+        for (int v = 0; v < d; ++v) {
+            bind[e.sum_letter] = v;
+            addends(P, *e.a, bind, G, sign, out);
+        }
+        if (shadow)
+            bind[e.sum_letter] = saved;
+        else
+            bind.erase(e.sum_letter);
+    } else {
+        out.push_back({sign, gen(P, e, bind, G)});
+    }
+}
+
+// A signed sum, emitted left to right after cancelling addends that are the same code with opposite
+// signs (e.g. the two bracket terms of Eq. 6 that name one stored element) and merging repeats into a
+// coefficient.
+std::string sum_code(std::vector<std::pair<int, std::string>> terms)
+{
+    std::vector<std::pair<int, std::string>> kept;
+    for (auto &t : terms) {
+        bool merged = false;
+        for (auto &k : kept)
+            if (k.second == t.second) {
+                k.first += t.first;
+                merged = true;
+                break;
+            }
+        if (!merged)
+            kept.push_back(t);
+    }
+    std::string s;
+    for (auto &k : kept) {
+        if (k.first == 0)
+            continue;
+        const int mag = k.first < 0 ? -k.first : k.first;
+        const bool pow2 = (mag & (mag - 1)) == 0 && mag <= 256;
+        int lg = 0;
+        while ((1 << lg) < mag)
+            ++lg;
+        const std::string term = mag == 1 ? k.second
+                                 : pow2   ? "tl_pow2(" + k.second + ", " + std::to_string(lg) + ")"
+                                          : "(" + std::to_string(mag) + ".0 * " + k.second + ")";
+        if (s.empty())
+            s = k.first < 0 ? "(-" + term + ")" : term;
+        else
+            s = "(" + s + (k.first < 0 ? " - " : " + ") + term + ")";
+    }
+    return s.empty() ? "(0.0)" : s;
+}
+
+std::string gen(const Program &P, const Expr &e, Binding &bind, GenState &G)
+{
+    switch (e.kind) {
+    case Expr::NUM:
+        return fmt_num(e.num);
+    case Expr::REF: {
+        const Tensor &t = P.tensors[e.tensor];
+        std::vector<int> tup;
+        for (size_t s = 0; s < e.idx.size(); ++s) {
+            int v = e.idx[s].fixed ? e.idx[s].value : bind.at(e.idx[s].letter) + e.idx[s].value;
+            if (v < 0 || v >= t.dims[s])
+                throw Error{"index of '" + t.name + "' out of range (offset or fixed index)"};
+            tup.push_back(v);
+        }
+        const int slot = t.slot_of.at(tup);
+        if (t.kind == 0)
+            G.used_inputs.insert(t.table_base + slot);
+        else if (!G.defined[e.tensor].count(slot))
+            throw Error{"component " + std::to_string(slot) + " of '" + t.name + "' is read before it is assigned"};
+        return value_name(P, e.tensor, slot);
+    }
+    case Expr::NEG:
+    case Expr::ADD:
+    case Expr::SUB:
+    case Expr::SUM: {
+        std::vector<std::pair<int, std::string>> terms;
+        addends(P, e, bind, G, 1, terms);
+        return sum_code(terms);
+    }
+    case Expr::MUL: {
+        // a constant factor +-2^k becomes an exact exponent adjustment on the integer pipe
+        for (int side = 0; side < 2; ++side) {
+            const Expr &c = side ? *e.b : *e.a;
+            const Expr &other = side ? *e.a : *e.b;
+            const bool neg = c.kind == Expr::NEG && c.a->kind == Expr::NUM;
+            const Expr &num = neg ? *c.a : c;
+            if (num.kind == Expr::NUM && num.num != 0.0) {
+                int k = 0;
+                const double m = frexp(num.num, &k);   // num = m 2^k, m in [0.5, 1)
+                if (m == 0.5 && k - 1 >= -8 && k - 1 <= 8 && k - 1 != 0) {
+                    const std::string v = gen(P, other, bind, G);
+                    const std::string scaled = "tl_pow2(" + v + ", " + std::to_string(k - 1) + ")";
+                    return neg ? "(-" + scaled + ")" : scaled;
+                }
+            }
+        }
+        return "(" + gen(P, *e.a, bind, G) + " * " + gen(P, *e.b, bind, G) + ")";
+    }
+    case Expr::DIV: {
+        // divisors are scalars: one reciprocal per distinct divisor, computed where first needed
+        const std::string den = gen(P, *e.b, bind, G);
+        auto it = G.recip.find(den);
+        if (it == G.recip.end()) {
+            const std::string name = "r_" + std::to_string(G.recip.size());
+            *G.body << "    const double " << name << " = 1.0 / " << den << ";\n";
+            it = G.recip.emplace(den, name).first;
+        }
+        return "(" + gen(P, *e.a, bind, G) + " * " + it->second + ")";
+    }
+    }
+    return "";
+}
+
+void generate(Program &P)
+{
+    // table layout: inputs then outputs, each tensor's stored components in storage order
+    P.n_in = P.n_out = 0;
+    std::ostringstream names;
+    for (auto &t : P.tensors)
+        if (t.kind == 0) {
+            t.table_base = P.n_in;
+            P.n_in += (int)t.stored.size();
+        }
+    for (auto &t : P.tensors)
+        if (t.kind == 1) {
+            t.table_base = P.n_out;
+            P.n_out += (int)t.stored.size();
+        }
+    for (int pass = 0; pass < 2; ++pass)
+        for (auto &t : P.tensors)
+            if (t.kind == pass)
+                for (auto &tup : t.stored) {
+                    names << (pass == 0 ? "in " : "out ") << t.name;
+                    for (int v : tup)
+                        names << " " << v;
+                    names << "\n";
+                }
+    P.names = names.str();
+    if (P.n_out == 0)
+        throw Error{"the program declares no output"};
+    if (P.n_in + P.n_out > 480)
+        throw Error{"more than 480 component arrays"};
+
+    GenState G;
+    G.defined.resize(P.tensors.size());
+    std::ostringstream body;
+    G.body = &body;
+    for (auto &st : P.stmts) {
+        const Tensor &t = P.tensors[st.tensor];
+        std::map<char, int> free_rhs;
+        free_letters(P, *st.rhs, free_rhs, std::set<char>());
+        std::set<char> lhs_letters;
+        for (size_t s = 0; s < st.lhs.size(); ++s)
+            if (!st.lhs[s].fixed) {
+                if (st.lhs[s].value != 0)
+                    throw Error{"offsets are not allowed on the left-hand side"};
+                if (lhs_letters.count(st.lhs[s].letter))
+                    throw Error{"left-hand side of '" + t.name + "' repeats an index"};
+                lhs_letters.insert(st.lhs[s].letter);
+            }
+        std::set<char> rhs_letters;
+        for (auto &kv : free_rhs)
+            rhs_letters.insert(kv.first);
+        if (rhs_letters != lhs_letters)
+            throw Error{"free indices of the right-hand side differ from the left-hand side of '" + t.name + "'"};
+        // every LHS index assignment whose tuple is a stored component
+        std::vector<char> letters(lhs_letters.begin(), lhs_letters.end());
+        std::vector<int> extent;
+        for (char l : letters)
+            for (size_t s = 0; s < st.lhs.size(); ++s)
+                if (!st.lhs[s].fixed && st.lhs[s].letter == l) {
+                    extent.push_back(range_of(P, l, t.dims[s]));
+                    break;
+                }
+        std::vector<int> val(letters.size(), 0);
+        std::vector<int> done_slots;
+        for (;;) {
+            Binding bind;
+            for (size_t q = 0; q < letters.size(); ++q)
+                bind[letters[q]] = val[q];
+            std::vector<int> tup;
+            for (auto &ix : st.lhs)
+                tup.push_back(ix.fixed ? ix.value : bind[ix.letter]);
+            bool in_range = true;
+            for (size_t s = 0; s < tup.size(); ++s)
+                in_range &= tup[s] >= 0 && tup[s] < t.dims[s];
+            if (!in_range)
+                throw Error{"fixed index out of range on the left-hand side of '" + t.name + "'"};
+            const int slot = t.slot_of.at(tup);
+            if (std::find(done_slots.begin(), done_slots.end(), slot) == done_slots.end()) {
+                std::string rhs = gen(P, *st.rhs, bind, G);
+                body << "    const double " << value_name(P, st.tensor, slot) << "_s" << &st - &P.stmts[0] << " = " << rhs
+                     << ";\n";
+                done_slots.push_back(slot);
+            }
+            int r = (int)letters.size() - 1;
+            while (r >= 0 && ++val[r] == extent[r])
+                val[r--] = 0;
+            if (r < 0)
+                break;
+        }
+        // publish this statement's values under the tensor's component names
+        for (int slot : done_slots) {
+            body << "    " << (G.defined[st.tensor].count(slot) ? "" : "double ") << value_name(P, st.tensor, slot)
+                 << " = " << value_name(P, st.tensor, slot) << "_s" << &st - &P.stmts[0] << ";\n";
+            G.defined[st.tensor].insert(slot);
+        }
+    }
+    for (auto &t : P.tensors)
+        if (t.kind == 1)
+            for (size_t slot = 0; slot < t.stored.size(); ++slot)
+                if (!G.defined[&t - &P.tensors[0]].count((int)slot))
+                    throw Error{"output component " + std::to_string(slot) + " of '" + t.name + "' is never assigned"};
+
+    std::ostringstream src;
+    src << "// generated from a tensor-index program; one thread per grid point\n"
+        << "// x * 2^k (|k| <= 8) by adjusting the exponent field with an integer add; zero, subnormal, huge,\n"
+        << "// inf and nan operands take the multiplication\n"
+        << "__device__ __forceinline__ double tl_pow2(double x, int k)\n{\n"
+        << "  const int hi = __double2hiint(x), lo = __double2loint(x);\n"
+        << "  const unsigned e = ((unsigned)hi >> 20) & 0x7ffu;\n"
+        << "  if (e > 8u && e < 2047u - 8u) { int r; asm(\"add.s32 %0, %1, %2;\" : \"=r\"(r) : \"r\"(hi), \"r\"(k << 20));\n"
+        << "    return __hiloint2double(r, lo); }\n"
+        << "  if (((hi & 0x7fffffff) | lo) == 0) return x;\n"
+        << "  return x * __hiloint2double((1023 + k) << 20, 0);\n}\n"
+        << "struct TlJitArgs { const double *in[" << std::max(P.n_in, 1) << "]; double *out[" << P.n_out << "]; };\n"
+        << "extern \"C\" __global__ void __launch_bounds__(256) tl_jit_kernel(const TlJitArgs a, long long n)\n{\n"
+        << "  for (long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x; x < n;\n"
+        << "       x += (long long)gridDim.x * blockDim.x) {\n";
+    for (auto &t : P.tensors)
+        if (t.kind == 0)
+            for (size_t slot = 0; slot < t.stored.size(); ++slot)
+                if (G.used_inputs.count(t.table_base + (int)slot))
+                    src << "    const double " << value_name(P, &t - &P.tensors[0], (int)slot) << " = __ldcs(a.in["
+                        << t.table_base + slot << "] + x);\n";
+    src << "    asm volatile(\"\" ::: \"memory\");\n" << body.str();
+    for (auto &t : P.tensors)
+        if (t.kind == 1)
+            for (size_t slot = 0; slot < t.stored.size(); ++slot)
+                src << "    __stcs(a.out[" << t.table_base + slot << "] + x, "
+                    << value_name(P, &t - &P.tensors[0], (int)slot) << ");\n";
+    src << "  }\n}\n";
+    P.source = src.str();
+}
+
+// ---------------------------------------------------------------------------------------------- NVRTC
+typedef int (*nvrtcCreateProgram_t)(void **, const char *, const char *, int, const char *const *, const char *const *);
+typedef int (*nvrtcCompileProgram_t)(void *, int, const char *const *);
+typedef int (*nvrtcGetSize_t)(void *, size_t *);
+typedef int (*nvrtcGetData_t)(void *, char *);
+typedef int (*nvrtcDestroyProgram_t)(void **);
+
+struct Nvrtc {
+    bool tried = false, ok = false;
+    nvrtcCreateProgram_t create = nullptr;
+    nvrtcCompileProgram_t compile = nullptr;
+    nvrtcGetSize_t log_size = nullptr, cubin_size = nullptr;
+    nvrtcGetData_t log = nullptr, cubin = nullptr;
+    nvrtcDestroyProgram_t destroy = nullptr;
+};
+Nvrtc g_nvrtc;
+std::mutex g_nvrtc_mu;
+
+bool load_nvrtc(std::string &why)
+{
+    std::lock_guard<std::mutex> lk(g_nvrtc_mu);
+    if (!g_nvrtc.tried) {
+        g_nvrtc.tried = true;
+        const char *cands[] = {"libnvrtc.so.13", "libnvrtc.so", "/usr/local/cuda/lib64/libnvrtc.so.13",
+                               "/usr/local/cuda/lib64/libnvrtc.so"};
+        void *h = nullptr;
+        for (const char *c : cands)
+            if ((h = dlopen(c, RTLD_NOW | RTLD_LOCAL)))
+                break;
+        if (h) {
+            g_nvrtc.create = (nvrtcCreateProgram_t)dlsym(h, "nvrtcCreateProgram");
+            g_nvrtc.compile = (nvrtcCompileProgram_t)dlsym(h, "nvrtcCompileProgram");
+            g_nvrtc.log_size = (nvrtcGetSize_t)dlsym(h, "nvrtcGetProgramLogSize");
+            g_nvrtc.log = (nvrtcGetData_t)dlsym(h, "nvrtcGetProgramLog");
+            g_nvrtc.cubin_size = (nvrtcGetSize_t)dlsym(h, "nvrtcGetCUBINSize");
+            g_nvrtc.cubin = (nvrtcGetData_t)dlsym(h, "nvrtcGetCUBIN");
+            g_nvrtc.destroy = (nvrtcDestroyProgram_t)dlsym(h, "nvrtcDestroyProgram");
+            g_nvrtc.ok = g_nvrtc.create && g_nvrtc.compile && g_nvrtc.log_size && g_nvrtc.log && g_nvrtc.cubin_size &&
+                         g_nvrtc.cubin && g_nvrtc.destroy;
+        }
+    }
+    if (!g_nvrtc.ok)
+        why = "NVRTC (libnvrtc.so.13) could not be loaded";
+    return g_nvrtc.ok;
+}
+
+bool nvrtc_compile(const std::string &src, std::vector<char> &cubin, std::string &log)
+{
+    if (!load_nvrtc(log))
+        return false;
+    void *prog = nullptr;
+    if (g_nvrtc.create(&prog, src.c_str(), "tl_jit.cu", 0, nullptr, nullptr) != 0) {
+        log = "nvrtcCreateProgram failed";
+        return false;
+    }
+    const char *opts[] = {"--gpu-architecture=sm_103a", "-std=c++17", "-default-device"};
+    const int rc = g_nvrtc.compile(prog, 3, opts);
+    size_t ls = 0;
+    g_nvrtc.log_size(prog, &ls);
+    log.assign(ls, '\0');
+    if (ls)
+        g_nvrtc.log(prog, &log[0]);
+    while (!log.empty() && log.back() == '\0')   // the reported size counts the terminator
+        log.pop_back();
+    bool ok = rc == 0;
+    if (ok) {
+        size_t cs = 0;
+        ok = g_nvrtc.cubin_size(prog, &cs) == 0 && cs > 0;
+        if (ok) {
+            cubin.resize(cs);
+            ok = g_nvrtc.cubin(prog, cubin.data()) == 0;
+        }
+    }
+    g_nvrtc.destroy(&prog);
+    return ok;
+}
+
+}  // namespace jit
+}  // namespace tl
+
+struct tl_jit_kernel {
+    uint64_t magic = 0;
+    tl::jit::Program prog;
+    std::vector<char> cubin;
+    std::mutex mu;
+    cudaLibrary_t lib[tl::kMaxDevices] = {};
+    cudaKernel_t kern[tl::kMaxDevices] = {};
+    int blocks[tl::kMaxDevices] = {};
+};
+
+using namespace tl;
+static constexpr uint64_t kJitMagic = 0x746c5f6a69743031ull;
+
+extern "C" {
+
+tl_status tl_jit_compile(const char *program, tl_jit_kernel **out, char *log, size_t log_size)
+{
+    if (log && log_size)
+        log[0] = '\0';
+    if (!program || !out)
+        return fail(TL_ERR_INVALID_ARG, "NULL program or output");
+    *out = nullptr;
+    auto k = std::make_unique<tl_jit_kernel>();
+    std::string why;
+    bool ok = false;
+    try {
+        const std::string text(program);   // the parser keeps a reference: it must outlive ps
+        jit::Parser ps(text, k->prog);
+        ps.parse();
+        jit::generate(k->prog);
+        ok = true;
+    } catch (const jit::Error &e) {
+        why = e.msg;
+    }
+    if (ok && !jit::nvrtc_compile(k->prog.source, k->cubin, why)) {
+        ok = false;
+        why = "NVRTC: " + why;
+    }
+    if (!ok) {
+        if (log && log_size)
+            snprintf(log, log_size, "%s", why.c_str());
+        return fail(TL_ERR_INVALID_ARG, "%s", why.c_str());
+    }
+    k->magic = kJitMagic;
+    *out = k.release();
+    return TL_OK;
+}
+
+tl_status tl_jit_info(const tl_jit_kernel *k, int32_t *n_in, int32_t *n_out, const char **source,
+                      const char **component_names)
+{
+    if (!k || k->magic != kJitMagic)
+        return fail(TL_ERR_INVALID_ARG, "not a compiled program");
+    if (n_in)
+        *n_in = k->prog.n_in;
+    if (n_out)
+        *n_out = k->prog.n_out;
+    if (source)
+        *source = k->prog.source.c_str();
+    if (component_names)
+        *component_names = k->prog.names.c_str();
+    return TL_OK;
+}
+
+tl_status tl_jit_launch(tl_jit_kernel *k, const double *const *in, double *const *out, int64_t n, tl_stream stream)
+{
+    if (!k || k->magic != kJitMagic)
+        return fail(TL_ERR_INVALID_ARG, "not a compiled program");
+    if ((k->prog.n_in && !in) || !out)
+        return fail(TL_ERR_INVALID_ARG, "NULL table");
+    if (n < 0)
+        return fail(TL_ERR_INVALID_ARG, "n = %lld < 0", (long long)n);
+    const void *const *tabs[2] = {(const void *const *)in, (const void *const *)out};
+    const int counts[2] = {k->prog.n_in, k->prog.n_out};
+    const bool writes[2] = {false, true}, nullable[2] = {false, false};
+    const char *const names[2] = {"in", "out"};
+    std::vector<Range> rs;
+    tl_status s = collect_ranges(rs, tabs, counts, writes, nullable, names, 2, n, sizeof(double), -1);
+    if (s == TL_OK)
+        s = check_overlaps(rs);
+    if (s != TL_OK || n == 0)
+        return s;
+    const DeviceInfo *d = nullptr;
+    if ((s = device_info(&d)) != TL_OK)
+        return s;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaError_t e;
+    {
+        std::lock_guard<std::mutex> lk(k->mu);
+        if (!k->kern[dev]) {   // load the module on this device once
+            if ((e = cudaLibraryLoadData(&k->lib[dev], k->cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0)) !=
+                cudaSuccess)
+                return cuda_fail(e, "cudaLibraryLoadData");
+            if ((e = cudaLibraryGetKernel(&k->kern[dev], k->lib[dev], "tl_jit_kernel")) != cudaSuccess)
+                return cuda_fail(e, "cudaLibraryGetKernel");
+            if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k->blocks[dev], (const void *)k->kern[dev], 256, 0)) !=
+                cudaSuccess)
+                return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+        }
+    }
+    std::vector<const void *> argbuf((size_t)std::max(k->prog.n_in, 1) + k->prog.n_out, nullptr);
+    for (int q = 0; q < k->prog.n_in; ++q)
+        argbuf[q] = in[q];
+    for (int q = 0; q < k->prog.n_out; ++q)
+        argbuf[std::max(k->prog.n_in, 1) + q] = out[q];
+    long long nn = (long long)n;
+    void *args[2] = {argbuf.data(), &nn};
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)d->sms * std::max(1, k->blocks[dev])));
+    if ((e = cudaLaunchKernel((const void *)k->kern[dev], dim3(grid), dim3(256), args, 0, (cudaStream_t)stream)) !=
+        cudaSuccess)
+        return cuda_fail(e, "generated kernel launch");
+    return TL_OK;
+}
+
+void tl_jit_destroy(tl_jit_kernel *k)
+{
+    if (!k || k->magic != kJitMagic)
+        return;
+    for (int dv = 0; dv < kMaxDevices; ++dv)
+        if (k->lib[dv])
+            cudaLibraryUnload(k->lib[dv]);
+    k->magic = 0;
+    delete k;
+}
+
+}  // extern "C"

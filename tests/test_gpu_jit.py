@@ -1,0 +1,66 @@
+"""Kernels emitted by the runtime generator against the reference interpreter of the same programs,
+and the generated metric-evolution chain against the chain oracle and the hand-written kernel."""
+import numpy as np
+import pytest
+
+import gridgen
+import oracle
+from oracle.tensor_expr import Program
+from tests.jit_programs import PROGRAMS
+from tests.parity import TOL_F64, assert_components, component_errors
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def dev():
+    return torch.device("cuda", 0)
+
+
+@pytest.mark.parametrize("name", sorted(PROGRAMS))
+@pytest.mark.parametrize("n", [1, 1000, 65537])
+def test_generated_kernel_matches_interpreter(name, n):
+    import paper_1804_10120_gb300 as tl
+    k = tl.JitKernel(PROGRAMS[name])
+    p = Program(PROGRAMS[name])
+    if name == "chain":
+        x = gridgen.random_grid(n, 71)
+    else:
+        x = gridgen.normal_fields(k.n_in, n, 71, 6000)
+    y = k.launch(torch.from_numpy(x).to(dev()))
+    torch.cuda.synchronize()
+    y = y.cpu().numpy()
+    ref = p.run(x)
+    # generated code may contract a*b + c into an FMA: compare per component against the
+    # component's scale (1e-12 for the chain, the 43-input program with a division)
+    tol = TOL_F64 if name == "chain" else 1e-13
+    assert component_errors(y, ref).max() <= tol, name
+    k.close()
+
+
+def test_generated_chain_equals_chain_oracle_and_hand_kernel():
+    import paper_1804_10120_gb300 as tl
+    k = tl.JitKernel(PROGRAMS["chain"])
+    x = gridgen.random_grid(1 << 20, 1)
+    xd = torch.from_numpy(x).to(dev())
+    y_gen = k.launch(xd)
+    y_hand = tl.tl_dtg_forward(xd)
+    torch.cuda.synchronize()
+    idx = np.random.default_rng(0).integers(0, 1 << 20, 20000)
+    ref = oracle.forward(np.ascontiguousarray(x[:, idx]))
+    assert_components(y_gen[:, idx].cpu().numpy(), ref, TOL_F64, what="generated chain")
+    assert component_errors(y_gen.cpu().numpy(), y_hand.cpu().numpy()).max() <= TOL_F64
+
+
+def test_empty_launch_and_reuse_across_streams():
+    import paper_1804_10120_gb300 as tl
+    k = tl.JitKernel(PROGRAMS["eq21"])
+    y = k.launch(torch.empty((10, 0), dtype=torch.float64, device=dev()))
+    assert y.shape == (6, 0)
+    x = torch.from_numpy(gridgen.normal_fields(10, 5000, 3, 6000)).to(dev())
+    s = torch.cuda.Stream()
+    y1 = k.launch(x)
+    y2 = k.launch(x, stream=s)
+    s.synchronize()
+    torch.cuda.synchronize()
+    assert torch.equal(y1, y2)
