@@ -59,25 +59,39 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def src_digest():
+# The source files that define each profiled kernel (its own translation unit and the headers it uses).
+_COMMON = ["tl_common.cuh", "tl_kernels.h"]
+KERNEL_SOURCES = {
+    "dtg_fwd_f64_kernel": ["dtg_fwd.cu", "dtg_fwd_body.cuh", "dtg_batched.cuh"] + _COMMON,
+    "dtg_fwd_f32_kernel": ["dtg_fwd.cu", "dtg_fwd_body.cuh", "dtg_batched.cuh"] + _COMMON,
+    "dtg_fwd_ff_kernel": ["dtg_fwd_ff.cu", "dtg_fwd_body.cuh", "ff.cuh", "dtg_batched.cuh"] + _COMMON,
+    "dtg_bwd_f64_kernel": ["dtg_bwd.cu", "dtg_fwd_body.cuh", "ff.cuh"] + _COMMON,
+    "dtg_bwd_ff_kernel": ["dtg_bwd.cu", "dtg_fwd_body.cuh", "ff.cuh"] + _COMMON,
+    "dtg_batched_f64_kernel": ["dtg_fwd.cu", "dtg_fwd_body.cuh", "dtg_batched.cuh"] + _COMMON,
+}
+
+
+def src_digest(kernel=None):
+    """Digest of a kernel's source files (all kernel sources when kernel is None)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1804_10120_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(csrc, name), "rb") as f:
-                h.update(name.encode() + f.read())
+    names = sorted(KERNEL_SOURCES[kernel]) if kernel else sorted(
+        n for n in os.listdir(csrc) if n.endswith((".cu", ".cuh", ".h")))
+    for name in names:
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode() + f.read())
     return h.hexdigest()[:16]
 
 
 def traffic_per_launch(kernel, n):
-    """DRAM bytes per launch from the committed ncu summary, scaled to n points; None when the kernel
+    """DRAM bytes per launch from the committed ncu summary, scaled to n points; None when the kernel's
     sources changed since the capture (or none exists)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(p) as f:
             d = json.load(f)
         e = d[kernel]
-        if e.get("src_digest") != src_digest():
+        if e.get("src_digest") != src_digest(kernel):
             return None
         return float(e["dram_bytes"]) * n / float(e["n"])
     except Exception:
