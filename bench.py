@@ -347,6 +347,21 @@ def extras(dev, stream, steps, x64, hbm):
                       "ms_600_launches": ms_sep, "ms_600_launches_in_graph": ms_sepg}
     plan.close()
     del xs, ys
+    # the chain with its 27 derivative inputs formed on the grid (periodic 256^3, 4th-order differences)
+    fshape = (256, 256, 256)
+    fd_fields = torch.from_numpy(gridgen.periodic_fields(fshape, 1)).to(dev)
+    y = torch.empty((39, n), dtype=torch.float64, device=dev)
+    fh = tuple(1.0 / m for m in fshape)
+    for dt in ("f64", "f64_ff"):
+        for order in (2, 4):
+            ms_fd = cuda_time(lambda: tl.tl_dtg_forward_fd(fd_fields, fshape, fh, order, y, dtype=dt, stream=stream),
+                              steps, stream)
+            out["fd_forward_%s_order%d" % (dt, order)] = {
+                "workload": "periodic 256^3 grid (2^24 points), smooth Fourier-mode fields, seed 1",
+                "ms": ms_fd, "points_per_s": n / ms_fd * 1e3, "GB_s": 440 * n / ms_fd / 1e6,
+                "hbm_frac": 440 * n / ms_fd / 1e6 / hbm,
+                "bytes_per_point": "16 arrays read + 39 written = 440"}
+    del fd_fields, y
     # the same chain written as a tensor-index program, emitted and compiled at run time
     from tests.jit_programs import PROGRAMS
     k = tl.JitKernel(PROGRAMS["chain"])

@@ -45,6 +45,8 @@ def lib():
             L.gridgen_normal.argtypes = [u64, u64, i64, i64, d, d, P]
             L.gridgen_random_grid.argtypes = [u64, u64, i64, i64, ctypes.POINTER(P)]
             L.gridgen_conformal_grid.argtypes = [i64, d, d, i64, i64, ctypes.POINTER(P)]
+            L.gridgen_periodic_fields.argtypes = [u64, i64, i64, i64, i64, i64, ctypes.POINTER(P)]
+            L.gridgen_periodic_fields.restype = None
             for f in (L.gridgen_uniform, L.gridgen_normal, L.gridgen_random_grid, L.gridgen_conformal_grid):
                 f.restype = None
             _lib = L
@@ -137,3 +139,21 @@ def subgrid_sides(count, seed, lo=8, hi=48, stream=4095):
     L = lib()
     span = hi - lo + 1
     return [lo + int(L.gridgen_bits(seed, stream, d) % span) for d in range(count)]
+
+
+def periodic_fields(shape, seed, out=None, threads=None):
+    """[16, nx*ny*nz] smooth periodic fields g[6], K[6], alpha, beta[3] on the unit box (x fastest)."""
+    nx, ny, nz = shape
+    n = nx * ny * nz
+    if out is None:
+        out = np.empty((16, n), dtype=np.float64)
+    L = lib()
+    P = ctypes.POINTER(ctypes.c_double)
+
+    def job(a, b):
+        def f():
+            tab = (P * 16)(*[_ptr(out[s], a) for s in range(16)])
+            L.gridgen_periodic_fields(seed, nx, ny, nz, a, b - a, tab)
+        return f
+    _run([job(a, b) for a, b in _chunks(n, threads or default_threads()) if b > a])
+    return out

@@ -124,3 +124,41 @@ void gridgen_conformal_grid(int64_t side, double lo, double hi, int64_t offset, 
             out[s][t] = 0.0;
     }
 }
+
+/*
+ * Smooth periodic fields on an nx x ny x nz grid over the unit box (x fastest, coordinate a / n per
+ * axis), 16 arrays laid out as g[6], K[6], alpha, beta[3]: each field is base + amp * sum of three
+ * Fourier modes a_m sin(2 pi k_m . x + phi_m), with integer wavevectors k_m (components in [-3, 3]),
+ * a_m ~ U[-1/3, 1/3] and phi_m ~ U[0, 2 pi) drawn from (seed, field).  g: base delta_ij, amp 0.05
+ * (diagonal >= 0.95, off-diagonal <= 0.05: SPD); K, beta: amp 0.1; alpha: base 1, amp 0.2.
+ * Writes points offset .. offset+n-1.
+ */
+void gridgen_periodic_fields(uint64_t seed, int64_t nx, int64_t ny, int64_t nz, int64_t offset, int64_t n,
+                             double *const out[16])
+{
+    static const int diag[6] = {1, 0, 0, 1, 0, 1};
+    double k[16][3][3], am[16][3], ph[16][3], base[16], amp[16];
+    for (int f = 0; f < 16; ++f) {
+        const uint64_t key = stream_key(seed, 8192 + (uint64_t)f);
+        for (int m = 0; m < 3; ++m) {
+            for (int d = 0; d < 3; ++d)
+                k[f][m][d] = (double)((int)(mix(key + (uint64_t)(16 * m + d + 1) * GG_GOLDEN) % 7) - 3);
+            am[f][m] = (2.0 * unif(key, 100 + m) - 1.0) / 3.0;
+            ph[f][m] = 6.283185307179586 * unif(key, 200 + m);
+        }
+        base[f] = f < 6 ? (double)diag[f] : (f == 12 ? 1.0 : 0.0);
+        amp[f] = f < 6 ? 0.05 : (f == 12 ? 0.2 : 0.1);
+    }
+    for (int64_t t = 0; t < n; ++t) {
+        const int64_t x = offset + t;
+        const double c[3] = {(double)(x % nx) / (double)nx, (double)((x / nx) % ny) / (double)ny,
+                             (double)(x / (nx * ny)) / (double)nz};
+        for (int f = 0; f < 16; ++f) {
+            double s = 0.0;
+            for (int m = 0; m < 3; ++m)
+                s += am[f][m] * sin(6.283185307179586 * (k[f][m][0] * c[0] + k[f][m][1] * c[1] + k[f][m][2] * c[2]) +
+                                    ph[f][m]);
+            out[f][t] = base[f] + amp[f] * s;
+        }
+    }
+}

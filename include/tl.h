@@ -210,6 +210,20 @@ TL_API tl_status tl_jit_launch(tl_jit_kernel *kernel, const double *const *in, d
                                tl_stream stream);
 TL_API void tl_jit_destroy(tl_jit_kernel *kernel);
 
+TL_API /*
+ * The forward chain with the spatial derivatives formed on the grid instead of read: d_k g_ij and
+ * d_j beta_i by centred finite differences of order 2 or 4 on a periodic nx x ny x nz grid (x fastest:
+ * point (ix, iy, iz) is element ix + nx (iy + ny iz) of every array), spacings hx, hy, hz.  The paper
+ * takes the derivatives as inputs (Listing 3); here one launch reads 16 arrays -- g[6], K[6], alpha,
+ * beta[3], layout as in tl_dtg_in -- and writes the 39 outputs of tl_dtg_forward, whose d_k g_ij and
+ * d_j beta_i are these differences.  dtype TL_F64 or TL_F64_FF (TL_ERR_UNSUPPORTED otherwise); other
+ * rules as for tl_dtg_forward.
+ */
+typedef struct { const void *g[6], *K[6], *alpha, *beta[3]; } tl_dtg_grid_in;
+typedef struct { int64_t nx, ny, nz; double hx, hy, hz; int32_t order; } tl_grid3d;
+TL_API tl_status tl_dtg_forward_fd(const tl_dtg_grid_in *in, const tl_dtg_out *out, const tl_grid3d *grid,
+                                   tl_dtype dtype, tl_stream stream);
+
 TL_API const char *tl_status_string(tl_status s);
 TL_API const char *tl_last_error(void);
 /* Library version as MAJOR*10000 + MINOR*100 + PATCH. */

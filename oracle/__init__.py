@@ -25,6 +25,7 @@ N_OUT = 39
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "dtg_oracle.c")
 _SRC_EXPR = os.path.join(_HERE, "expr_oracle.c")
+_SRC_FD = os.path.join(_HERE, "fd_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -32,12 +33,12 @@ _lib = None
 
 def build(force=False):
     """Compile liboracle.so with gcc (plain C99, -O2, no FP contraction)."""
-    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= max(os.path.getmtime(_SRC),
-                                                                            os.path.getmtime(_SRC_EXPR)):
+    srcs = [_SRC, _SRC_EXPR, _SRC_FD]
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= max(os.path.getmtime(f) for f in srcs):
         return _LIB
     tmp = _LIB + ".tmp%d" % os.getpid()
     subprocess.check_call(["gcc", "-std=c99", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
-                           "-shared", "-o", tmp, _SRC, _SRC_EXPR, "-lm"])
+                           "-shared", "-o", tmp] + srcs + ["-lm"])
     os.replace(tmp, _LIB)
     return _LIB
 
@@ -55,6 +56,10 @@ def lib():
             L.oracle_metric_det.argtypes = [ctypes.POINTER(P), P, ctypes.c_int64]
             L.oracle_expr.argtypes = [ctypes.c_int, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.c_int64]
             L.oracle_expr.restype = ctypes.c_int
+            L.oracle_fd_inputs.argtypes = [ctypes.POINTER(P), ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                           ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                           ctypes.POINTER(P)]
+            L.oracle_fd_inputs.restype = ctypes.c_int
             for f in (L.oracle_dtg_forward, L.oracle_dtg_backward, L.oracle_metric_det):
                 f.restype = ctypes.c_int
             _lib = L
@@ -163,4 +168,21 @@ def expr(eq, inputs):
     rc = lib().oracle_expr(eq, _table(rows, n_in, n), _table(orows, n_out, n), n)
     if rc != 0:
         raise ValueError("oracle_expr rejected its arguments")
+    return out
+
+
+def fd_inputs(fields16, shape, spacing, order):
+    """The 43-array chain input table from the 16 arrays g[6], K[6], alpha, beta[3] on a periodic grid
+    of shape (nx, ny, nz) (x fastest) with spacings (hx, hy, hz): derivatives by centred differences of
+    the given order (2 or 4)."""
+    rows = _rows(fields16, 16)
+    nx, ny, nz = shape
+    n = nx * ny * nz
+    assert rows[0].shape[0] == n
+    out = np.empty((N_IN, n), dtype=np.float64)
+    orows = [out[s] for s in range(N_IN)]
+    rc = lib().oracle_fd_inputs(_table(rows, 16, n), nx, ny, nz, spacing[0], spacing[1], spacing[2], order,
+                                _table(orows, N_IN, n))
+    if rc != 0:
+        raise ValueError("oracle_fd_inputs rejected its arguments")
     return out

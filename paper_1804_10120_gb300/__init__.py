@@ -484,3 +484,36 @@ class JitKernel:
 
 def tl_jit_compile(program):
     return JitKernel(program)
+
+
+# ------------------------------------------------------------------------------ on-grid derivatives
+
+class _Grid3d(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int64), ("ny", ctypes.c_int64), ("nz", ctypes.c_int64), ("hx", ctypes.c_double),
+                ("hy", ctypes.c_double), ("hz", ctypes.c_double), ("order", ctypes.c_int32)]
+
+
+def tl_dtg_forward_fd(fields, shape, spacing, order=4, outputs=None, dtype="f64", stream=None):
+    """Forward chain with d_k g_ij and d_j beta_i by centred differences (order 2 or 4) on a periodic
+    grid of shape (nx, ny, nz), x fastest, spacings (hx, hy, hz).  fields: [16, n] device float64
+    (g[6], K[6], alpha, beta[3]).  Returns the [39, n] outputs of tl_dtg_forward."""
+    import torch
+    code = _dtype_code(dtype)
+    rows = _rows(fields, 16, "fields")
+    n = rows[0].shape[0]
+    if n != shape[0] * shape[1] * shape[2]:
+        raise ValueError("fields hold %d points, shape %s has %d" % (n, shape, shape[0] * shape[1] * shape[2]))
+    dev = rows[0].device
+    if outputs is None:
+        outputs = torch.empty((N_OUT, n), dtype=torch.float64, device=dev)
+    orows = _rows(outputs, N_OUT, "outputs")
+    itab = _table(rows, 16, n, torch.float64, "cuda", "fields")
+    otab = _table(orows, N_OUT, n, torch.float64, "cuda", "outputs")
+    g = _Grid3d(shape[0], shape[1], shape[2], spacing[0], spacing[1], spacing[2], order)
+    L = lib()
+    L.tl_dtg_forward_fd.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
+    L.tl_dtg_forward_fd.restype = ctypes.c_int
+    with torch.cuda.device(dev):
+        _check(L.tl_dtg_forward_fd(ctypes.byref(itab), ctypes.byref(otab), ctypes.byref(g), code,
+                                   _stream_handle(stream, dev)))
+    return outputs

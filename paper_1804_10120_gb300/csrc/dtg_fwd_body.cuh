@@ -39,13 +39,11 @@ __device__ __forceinline__ void christoffel_bracket(const R (&dg)[18], R (&T)[3]
 }
 
 // ------------------------------------------------------------------------------------ binary64 forward
-__device__ __forceinline__ void fwd_point_f64(const FwdArgs<double> &a, int64_t x)
+// The chain on one point's 43 input values (already in registers, in the input-table order); the 39
+// outputs go to o.out[s][x] (o: any argument block with an `out` table).
+template <class OutTable>
+__device__ __forceinline__ void chain_f64(const double (&v)[N_IN], const OutTable &o, int64_t x)
 {
-    double v[N_IN];
-#pragma unroll
-    for (int s = 0; s < N_IN; ++s)
-        v[s] = ld_stream(a.in[s] + x);
-    asm volatile("" ::: "memory");   // every load is issued before any arithmetic
     // step 1: inverse metric by cofactors; det by first-row expansion
     const double g00 = v[IN_G + 0], g01 = v[IN_G + 1],
                  g02 = v[IN_G + 2], g11 = v[IN_G + 3],
@@ -69,7 +67,7 @@ __device__ __forceinline__ void fwd_point_f64(const FwdArgs<double> &a, int64_t 
     for (int p = 0; p < 6; ++p) {
         ginv[p] = c[p] * rdet;
         h[p] = half_exact(ginv[p]);          // 1/2 g^il of Eq. 6
-        st_stream(a.out[OUT_GINV + p] + x, ginv[p]);
+        st_stream(o.out[OUT_GINV + p] + x, ginv[p]);
     }
 
     // step 2: Christoffel symbols, Eq. 6
@@ -81,7 +79,7 @@ __device__ __forceinline__ void fwd_point_f64(const FwdArgs<double> &a, int64_t 
 #pragma unroll
         for (int p = 0; p < 6; ++p) {
             gam[i][p] = fma(h[sym(i, 2)], T[2][p], fma(h[sym(i, 1)], T[1][p], h[sym(i, 0)] * T[0][p]));
-            st_stream(a.out[OUT_GAMMA + 6 * i + p] + x, gam[i][p]);
+            st_stream(o.out[OUT_GAMMA + 6 * i + p] + x, gam[i][p]);
         }
 
     // step 3: nabla_j beta_i = d_j beta_i - Gamma^k_ij beta_k
@@ -95,7 +93,7 @@ __device__ __forceinline__ void fwd_point_f64(const FwdArgs<double> &a, int64_t 
             const int p = sym(i, j);
             const double B = v[IN_DBETA + 3 * i + j];
             nb[i][j] = fma(-gam[2][p], b2, fma(-gam[1][p], b1, fma(-gam[0][p], b0, B)));
-            st_stream(a.out[OUT_DBCOV + 3 * i + j] + x, nb[i][j]);
+            st_stream(o.out[OUT_DBCOV + 3 * i + j] + x, nb[i][j]);
         }
 
     // step 4: Eq. 5, d_t g_ij = -2 alpha K_ij + nabla_i beta_j + nabla_j beta_i
@@ -107,8 +105,18 @@ __device__ __forceinline__ void fwd_point_f64(const FwdArgs<double> &a, int64_t 
             const int p = sym(i, j);
             const double K = v[IN_K + p];
             const double s = (i == j) ? twice_exact(nb[i][i]) : nb[i][j] + nb[j][i];
-            st_stream(a.out[OUT_DTG + p] + x, fma(m2a, K, s));
+            st_stream(o.out[OUT_DTG + p] + x, fma(m2a, K, s));
         }
+}
+
+__device__ __forceinline__ void fwd_point_f64(const FwdArgs<double> &a, int64_t x)
+{
+    double v[N_IN];
+#pragma unroll
+    for (int s = 0; s < N_IN; ++s)
+        v[s] = ld_stream(a.in[s] + x);
+    asm volatile("" ::: "memory");   // every load is issued before any arithmetic
+    chain_f64(v, a, x);
 }
 
 }  // namespace tl

@@ -14,6 +14,7 @@
 #include <algorithm>
 
 #include "../../include/tl_testing.h"
+#include "dtg_ff_body.cuh"
 #include "ff.cuh"
 #include "tl_kernels.h"
 
@@ -29,88 +30,8 @@ __device__ __forceinline__ void fwd_point_ff(const FwdArgs<double> &a, int64_t x
     for (int s = 0; s < N_IN; ++s)
         v[s] = ld_stream(a.in[s] + x);
     asm volatile("" ::: "memory");   // every load is issued before any arithmetic
-    const double g00 = v[IN_G + 0], g01 = v[IN_G + 1],
-                 g02 = v[IN_G + 2], g11 = v[IN_G + 3],
-                 g12 = v[IN_G + 4], g22 = v[IN_G + 5];
-    double dg[18];
-#pragma unroll
-    for (int s = 0; s < 18; ++s)
-        dg[s] = v[IN_DG + s];
-
-    // step 1 in binary64
-    double c[6];
-    c[0] = fma(g11, g22, -(g12 * g12));
-    c[1] = fma(g02, g12, -(g01 * g22));
-    c[2] = fma(g01, g12, -(g02 * g11));
-    c[3] = fma(g00, g22, -(g02 * g02));
-    c[4] = fma(g01, g02, -(g00 * g12));
-    c[5] = fma(g00, g11, -(g01 * g01));
-    const double det = fma(g00, c[0], fma(g01, c[1], g02 * c[2]));
-    const double rdet = rcp_f64(det);
-    uint32_t big = 0;
-    ff h[6];
-#pragma unroll
-    for (int p = 0; p < 6; ++p) {
-        const double gi = c[p] * rdet;
-        st_stream(a.out[OUT_GINV + p] + x, gi);
-        h[p] = split_ff(half_exact(gi), big);
-    }
-
-    // bracket of Eq. 6 in binary64, then pairs
-    double Td[3][6];
-    christoffel_bracket<double>(dg, Td);
-    ff T[3][6];
-#pragma unroll
-    for (int l = 0; l < 3; ++l)
-#pragma unroll
-        for (int p = 0; p < 6; ++p)
-            T[l][p] = split_ff(Td[l][p], big);
-
-    const double b0 = v[IN_BETA + 0], b1 = v[IN_BETA + 1],
-                 b2 = v[IN_BETA + 2];
-    const ff bf0 = split_ff(b0, big), bf1 = split_ff(b1, big), bf2 = split_ff(b2, big);
-
-    if (big) {   // outside the pair format's range: the all-binary64 evaluation of this point
+    if (!chain_ff(v, a, x))          // outside the pair format's range: all-binary64 evaluation
         fwd_point_f64_general(a, x);
-        return;
-    }
-
-    // step 2: Eq. 6 contraction in pairs
-    ff gam[3][6];
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int p = 0; p < 6; ++p) {
-            gam[i][p] = dot3_ff(h[sym(i, 0)], T[0][p], h[sym(i, 1)], T[1][p], h[sym(i, 2)], T[2][p]);
-            st_stream(a.out[OUT_GAMMA + 6 * i + p] + x, merge_ff(gam[i][p]));
-        }
-
-    // step 3: S_ij = Gamma^k_ij beta_k (symmetric in ij: 6 sums) in pairs, then
-    // nabla_j beta_i = d_j beta_i - S_ij in binary64 (exactly d_j beta_i where S vanishes)
-    double S6[6];
-#pragma unroll
-    for (int p = 0; p < 6; ++p)
-        S6[p] = merge_ff(dot3_ff(gam[0][p], bf0, gam[1][p], bf1, gam[2][p], bf2));
-    double nb[3][3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            nb[i][j] = v[IN_DBETA + 3 * i + j] - S6[sym(i, j)];
-            st_stream(a.out[OUT_DBCOV + 3 * i + j] + x, nb[i][j]);
-        }
-
-    // step 4: Eq. 5 in binary64
-    const double m2a = neg_exact(twice_exact(v[IN_ALPHA]));
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = i; j < 3; ++j) {
-            const int p = sym(i, j);
-            const double K = v[IN_K + p];
-            const double s = (i == j) ? twice_exact(nb[i][i]) : nb[i][j] + nb[j][i];
-            st_stream(a.out[OUT_DTG + p] + x, fma(m2a, K, s));
-        }
 }
 
 __global__ void __launch_bounds__(kFwdThreads) dtg_fwd_ff_kernel(const FwdArgs<double> a, int64_t n)
