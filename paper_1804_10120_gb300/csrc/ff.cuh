@@ -25,13 +25,6 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
     e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
-// a + b = s + e exactly when |a| >= |b| (or a == 0).
-__device__ __forceinline__ void fast_two_sum(float a, float b, float &s, float &e)
-{
-    s = __fadd_rn(a, b);
-    e = __fsub_rn(b, __fsub_rn(s, a));
-}
-
 // Split a binary64 value into hi (its leading 24 significant bits, truncated) and lo (the remaining 29
 // bits rounded to binary32): hi + lo = x within 2^-48 |x| (the pair carries 48 significant bits).  Magnitudes below 2^-74 lose lo and below
 // 2^-126 become zero (absolute error < 2^-97); `big` is set for |x| >= 2^63, infinities and NaN, which
