@@ -1,13 +1,14 @@
 // dtg_bwd.cu -- adjoint of the fused chain: given upstream gradients of the 39 outputs, the gradient of
 // L = sum gout * out with respect to the 43 stored inputs.  The paper has no adjoint; this is the
 // reverse-mode derivative of Eq. 5, the footnote to Listing 1, Eq. 6 and the inverse metric, taken in
-// reverse order.  g^ij, the bracket T of Eq. 6 and Gamma are recomputed in registers from the inputs
-// (never stored or re-read), so one launch reads 43 inputs plus the upstream gradients present and
-// writes 43 input gradients.
+// reverse order.  g^ij and the bracket T of Eq. 6 are recomputed in registers from the inputs (never
+// stored or re-read; Gamma itself is not needed, see betabar below), so one launch reads the inputs
+// the gradient depends on plus the upstream gradients present and writes 43 input gradients.
 //
 // Per point, with h = g^ij / 2, Gamma^i_p = sum_l h_il T_lp, Nbar the gradient of nabla_j beta_i:
 //   Kbar_p = -2 alpha W_p,  abar = -2 sum_p K_p W_p,  Nbar_ij = U_ij + (W_p(ij), doubled on the diagonal)
-//   dbetabar_ij = Nbar_ij,  S_p = Nbar_ij + Nbar_ji (i<j) or Nbar_ii,  betabar_k = -sum_p S_p Gamma^k_p
+//   dbetabar_ij = Nbar_ij,  S_p = Nbar_ij + Nbar_ji (i<j) or Nbar_ii,
+//   betabar_k = -sum_p S_p Gamma^k_p = -sum_l h_kl u_l,  u_l = sum_p S_p T_lp
 //   Gammabar_kp = V_kp - beta_k S_p
 //   Hbar_il = 1/2 sum_p Gammabar_ip T_lp (+ the g^ij upstream gradient on the stored entries)
 //   Tbar_lp = sum_i h_il Gammabar_ip, scattered through the bracket's three terms onto d_k g_ij
@@ -54,12 +55,6 @@ template <bool kU, bool kG> __device__ __forceinline__ void bwd_point_f64(const 
     }
     double T[3][6];
     christoffel_bracket<double>(dg, T);
-    double gam[3][6];
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int p = 0; p < 6; ++p)
-            gam[i][p] = fma(h[sym(i, 2)], T[2][p], fma(h[sym(i, 1)], T[1][p], h[sym(i, 0)] * T[0][p]));
 
     // ---- Eq. 5
     const double alpha = ld_stream(a.in[IN_ALPHA] + x);
@@ -100,15 +95,21 @@ template <bool kU, bool kG> __device__ __forceinline__ void bwd_point_f64(const 
         for (int p = 0; p < 6; ++p)
             S[p] = twice_exact(W[p]);
     }
-    double beta[3];
+    // betabar_k = -sum_p S_p Gamma^k_p = -sum_l h_kl u_l with u_l = sum_p S_p T_lp: Gamma itself is
+    // never needed by the adjoint
+    double u[3], beta[3];
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+        double s = S[0] * T[l][0];
+#pragma unroll
+        for (int p = 1; p < 6; ++p)
+            s = fma(S[p], T[l][p], s);
+        u[l] = s;
+    }
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         beta[k] = ld_stream(a.in[IN_BETA + k] + x);
-        double s = gam[k][0] * S[0];
-#pragma unroll
-        for (int p = 1; p < 6; ++p)
-            s = fma(gam[k][p], S[p], s);
-        st_stream(a.gin[IN_BETA + k] + x, -s);
+        st_stream(a.gin[IN_BETA + k] + x, -fma(h[sym(k, 2)], u[2], fma(h[sym(k, 1)], u[1], h[sym(k, 0)] * u[0])));
     }
 
     // ---- Gamma: Gammabar = V - beta_k S_p
@@ -198,8 +199,8 @@ template <bool kU, bool kG> __device__ __forceinline__ void bwd_point_f64(const 
 // ------------------------------------------------------------------------------ float-float adjoint
 // The binary64 adjoint needs ~330 FP64 operations per point (1/64-rate pipe on this part).  Here the
 // inverse, the bracket, Kbar, abar and the folds of the upstream gradients stay in binary64, and every
-// contraction -- Gamma, betabar, Gammabar, Hbar, Tbar, the bracket's scatter onto d_k g_ij and
-// -H A H -- runs in float-float pairs (ff.cuh); points with values the pairs cannot carry take the
+// contraction -- betabar, Gammabar, Hbar, Tbar, the bracket's scatter onto d_k g_ij and -H A H --
+// runs in float-float pairs (ff.cuh); points with values the pairs cannot carry take the
 // binary64 body.
 template <bool kU, bool kG>
 __device__ __noinline__ void bwd_point_f64_general(const BwdArgs<double> &a, int64_t x)
@@ -303,21 +304,21 @@ template <bool kU, bool kG> __device__ __forceinline__ void bwd_point_ff(const B
         return;
     }
 
-    // Gamma^k_p and betabar_k = -sum_p S_p Gamma^k_p
+    // betabar_k = -sum_p S_p Gamma^k_p = -sum_l h_kl u_l with u_l = sum_p S_p T_lp
+    ff uf[3];
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+        ffacc U = acc_prod(Sf[0], Tf[l][0]);
+#pragma unroll
+        for (int p = 1; p < 6; ++p)
+            acc_add_prod(U, Sf[p], Tf[l][p]);
+        uf[l] = acc_result(U);
+    }
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        ffacc B = ffacc{0.0f, 0.0f};
-#pragma unroll
-        for (int p = 0; p < 6; ++p) {
-            ffacc G = acc_prod(hf[sym(k, 0)], Tf[0][p]);
-            acc_add_prod(G, hf[sym(k, 1)], Tf[1][p]);
-            acc_add_prod(G, hf[sym(k, 2)], Tf[2][p]);
-            const ff gam = acc_result(G);
-            if (p == 0)
-                B = acc_prod(Sf[0], gam);
-            else
-                acc_add_prod(B, Sf[p], gam);
-        }
+        ffacc B = acc_prod(hf[sym(k, 0)], uf[0]);
+        acc_add_prod(B, hf[sym(k, 1)], uf[1]);
+        acc_add_prod(B, hf[sym(k, 2)], uf[2]);
         st_stream(a.gin[IN_BETA + k] + x, neg_exact(merge_ff(acc_result(B))));
     }
 
