@@ -850,7 +850,30 @@ bool load_nvrtc(std::string &why)
     return g_nvrtc.ok;
 }
 
+// Compiled images by generated source: programs that generate the same source compile once per process.
+std::map<std::string, std::vector<char>> g_cubin_cache;
+std::mutex g_cubin_mu;
+
+bool nvrtc_compile_uncached(const std::string &src, std::vector<char> &cubin, std::string &log);
+
 bool nvrtc_compile(const std::string &src, std::vector<char> &cubin, std::string &log)
+{
+    {
+        std::lock_guard<std::mutex> lk(g_cubin_mu);
+        auto it = g_cubin_cache.find(src);
+        if (it != g_cubin_cache.end()) {
+            cubin = it->second;
+            return true;
+        }
+    }
+    if (!nvrtc_compile_uncached(src, cubin, log))
+        return false;
+    std::lock_guard<std::mutex> lk(g_cubin_mu);
+    g_cubin_cache.emplace(src, cubin);
+    return true;
+}
+
+bool nvrtc_compile_uncached(const std::string &src, std::vector<char> &cubin, std::string &log)
 {
     if (!load_nvrtc(log))
         return false;
