@@ -372,6 +372,18 @@ def extras(dev, stream, steps, x64, hbm):
                               "ms": ms_gen, "points_per_s": n / ms_gen * 1e3, "GB_s": 656 * n / ms_gen / 1e6,
                               "hbm_frac": 656 * n / ms_gen / 1e6 / hbm}
     k.close()
+    # the same program unfused: one kernel per assigned tensor, then per stored component, with the
+    # intermediates through device memory (the paper's evaluation model and its "Arrays" baseline)
+    from paper_1804_10120_gb300.statements import StatementPipeline
+    for mode in ("statement", "component"):
+        pl = StatementPipeline(PROGRAMS["chain"], mode)
+        ms_st = cuda_time(lambda: pl.run(x64, y, stream=stream), steps, stream)
+        elems = pl.elements_per_point()
+        out["generated_chain"]["per_" + mode] = {
+            "launches": pl.launches, "ms": ms_st, "points_per_s": n / ms_st * 1e3,
+            "bytes_per_point": 8 * elems, "GB_s": 8 * elems * n / ms_st / 1e6,
+            "hbm_frac": 8 * elems * n / ms_st / 1e6 / hbm, "fused_speedup": ms_st / ms_gen}
+        pl.close()
     del y
     # the expression suite of Sec. 5.1 at a realistic multi-domain grid size and at a large one
     rows = suite(dev, stream, [32768, 1 << 22], reps=max(3, steps // 2))

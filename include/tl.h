@@ -206,6 +206,10 @@ typedef struct tl_jit_kernel tl_jit_kernel;
 TL_API tl_status tl_jit_compile(const char *program, tl_jit_kernel **kernel, char *log, size_t log_size);
 TL_API tl_status tl_jit_info(const tl_jit_kernel *kernel, int32_t *n_in, int32_t *n_out, const char **source,
                              const char **component_names);
+/* reads[q] (q < n_in) = 1 when the generated kernel loads input table entry q, 0 for a component of an
+ * `in` tensor that no statement references (its entry must still be a valid array: tl_jit_launch checks
+ * every entry).  Lets a caller count the kernel's algorithmic traffic.  `reads` is caller-owned. */
+TL_API tl_status tl_jit_reads(const tl_jit_kernel *kernel, uint8_t *reads);
 TL_API tl_status tl_jit_launch(tl_jit_kernel *kernel, const double *const *in, double *const *out, int64_t n,
                                tl_stream stream);
 TL_API void tl_jit_destroy(tl_jit_kernel *kernel);

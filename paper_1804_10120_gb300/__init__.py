@@ -452,6 +452,11 @@ class JitKernel:
         for line in names.value.decode().splitlines():
             kind, name, *idx = line.split()
             (self.inputs if kind == "in" else self.outputs).append((name, tuple(int(v) for v in idx)))
+        L.tl_jit_reads.argtypes = [vp, vp]
+        L.tl_jit_reads.restype = ctypes.c_int
+        flags = (ctypes.c_uint8 * max(self.n_in, 1))()
+        _check(L.tl_jit_reads(h, ctypes.cast(flags, vp)))
+        self.reads = [bool(flags[q]) for q in range(self.n_in)]    # input entries the kernel loads
 
     def launch(self, inputs, outputs=None, stream=None):
         import torch

@@ -80,6 +80,7 @@ struct Program {
     std::vector<Stmt> stmts;
     int n_in = 0, n_out = 0;
     std::string source, names;
+    std::vector<uint8_t> reads;                 // per input table entry: does the kernel load it
 };
 
 struct Error {
@@ -802,6 +803,9 @@ void generate(Program &P)
                     << value_name(P, &t - &P.tensors[0], (int)slot) << ");\n";
     src << "  }\n}\n";
     P.source = src.str();
+    P.reads.assign((size_t)P.n_in, 0);
+    for (int q : G.used_inputs)
+        P.reads[(size_t)q] = 1;
 }
 
 // ---------------------------------------------------------------------------------------------- NVRTC
@@ -968,6 +972,17 @@ tl_status tl_jit_info(const tl_jit_kernel *k, int32_t *n_in, int32_t *n_out, con
         *source = k->prog.source.c_str();
     if (component_names)
         *component_names = k->prog.names.c_str();
+    return TL_OK;
+}
+
+tl_status tl_jit_reads(const tl_jit_kernel *k, uint8_t *reads)
+{
+    if (!k || k->magic != kJitMagic)
+        return fail(TL_ERR_INVALID_ARG, "not a compiled program");
+    if (!reads && k->prog.n_in)
+        return fail(TL_ERR_INVALID_ARG, "NULL reads");
+    for (int q = 0; q < k->prog.n_in; ++q)
+        reads[q] = k->prog.reads[(size_t)q];
     return TL_OK;
 }
 

@@ -64,3 +64,31 @@ def test_empty_launch_and_reuse_across_streams():
     s.synchronize()
     torch.cuda.synchronize()
     assert torch.equal(y1, y2)
+
+
+
+UNFUSED = [("statement", name) for name in sorted(PROGRAMS)] + \
+          [("component", name) for name in ("chain", "eq14", "eq21", "listing17", "spatial_slice", "trace_div")]
+
+
+@pytest.mark.parametrize("mode,name", UNFUSED)
+def test_unfused_pipeline_matches_fused_and_interpreter(mode, name):
+    """The program evaluated one kernel per assigned tensor or per stored component (intermediates
+    through device memory, launched on a side stream) against the fused kernel and the reference
+    interpreter."""
+    from paper_1804_10120_gb300.statements import StatementPipeline
+    n = 65537
+    pl = StatementPipeline(PROGRAMS[name], mode)
+    x = gridgen.random_grid(n, 72) if name == "chain" else gridgen.normal_fields(pl.n_in, n, 72, 6000)
+    xd = torch.from_numpy(x).to(dev())
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    y_st = pl.run(xd, stream=s)
+    s.synchronize()
+    y_fused = pl.fused.launch(xd)
+    torch.cuda.synchronize()
+    tol = TOL_F64 if name == "chain" else 1e-13
+    ref = Program(PROGRAMS[name]).run(x)
+    assert component_errors(y_st.cpu().numpy(), ref).max() <= tol, name
+    assert component_errors(y_st.cpu().numpy(), y_fused.cpu().numpy()).max() <= tol, name
+    pl.close()

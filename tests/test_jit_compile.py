@@ -40,3 +40,57 @@ def test_chain_tables_match_the_fixed_abi(tl):
     assert k.inputs[30] == ("alpha", ())
     assert k.outputs[6 + 6 * 1 + 4] == ("Gamma", (1, 1, 2))
     assert k.outputs[24 + 3 * 2 + 1] == ("dbcov", (2, 1))
+
+
+
+UNFUSED = [("statement", name) for name in sorted(PROGRAMS)] + \
+          [("component", name) for name in ("chain", "eq14", "eq21", "listing17", "spatial_slice", "trace_div")]
+
+
+@pytest.mark.parametrize("mode,name", UNFUSED)
+def test_unfused_pipeline_routes_every_component(tl, mode, name):
+    """Unfused stages: every component a stage loads is an input of the program or written by an
+    earlier stage, and the stages together write every output of the fused kernel exactly once."""
+    from paper_1804_10120_gb300.statements import StatementPipeline
+    pl = StatementPipeline(PROGRAMS[name], mode)
+    written = set(pl.fused.inputs)
+    for k, keys in pl.stages:
+        assert all(key in written for key, rd in zip(k.inputs, k.reads) if rd), name
+        assert not (set(keys) & written), name
+        written |= set(keys)
+    assert set(pl.fused.outputs) <= written
+    pl.close()
+
+
+def test_unfused_pipelines_of_the_chain(tl):
+    """Per tensor the chain splits into c, det, ginv, T, Gamma, dbcov, dtg with 25 temporary
+    components (cofactors, determinant, bracket); per component it is 6+1+6+18+18+9+6 = 64 launches.
+    Loaded plus stored elements per point: 82 fused, 171 per tensor, 331 per component (e.g. each
+    Gamma component loads 3 ginv and 3 bracket components and stores 1)."""
+    from paper_1804_10120_gb300.statements import StatementPipeline, split_components
+    pl = StatementPipeline(PROGRAMS["chain"])
+    assert [k.outputs[0][0] for k, _ in pl.stages] == ["c", "det", "ginv", "T", "Gamma", "dbcov", "dtg"]
+    assert pl.intermediate_components() == 6 + 1 + 18
+    assert pl.fused.n_in + pl.fused.n_out == 82
+    assert pl.elements_per_point() == 171
+    pl.close()
+    pieces = split_components(PROGRAMS["chain"])
+    assert len(pieces) == 64
+    assert [key for key, _ in pieces].count(("Gamma", (2, 1, 2))) == 1
+    assert ("Gamma", (2, 2, 1)) not in [key for key, _ in pieces]
+    g212 = dict(pieces)[("Gamma", (2, 1, 2))]
+    assert "Sum(l, ginv(2,l)*T(l,1,2))" in g212
+    pl = StatementPipeline(PROGRAMS["chain"], "component")
+    assert pl.launches == 64 and pl.intermediate_components() == 25
+    assert pl.elements_per_point() == 331
+    pl.close()
+
+
+def test_component_split_of_fixed_and_offset_indices():
+    """listing17's D(i,0) = Sum(c, E(i+1,c) F(c,0)) over i < 3: the offset is resolved per component
+    and the fixed-index statements that follow keep their own components."""
+    from paper_1804_10120_gb300.statements import split_components
+    pieces = dict(split_components(PROGRAMS["listing17"]))
+    assert "Sum(c, E(3,c)*F(c,0))" in pieces[("D", (0, 2))]
+    assert "E(0,0)" in pieces[("D", (0, 3))]
+    assert len(pieces) == 10
