@@ -42,9 +42,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the measurements of the other forms")
-    ap.add_argument("--only", default=None, choices=["forward", "adjoint", "batched"],
+    ap.add_argument("--only", default=None, choices=["forward", "adjoint", "batched", "fd", "generated"],
                     help="run just one form on --n points (or --grids subgrids) and print its timing; for profiling")
     ap.add_argument("--grids", type=int, default=600)
+    ap.add_argument("--order", type=int, default=4, choices=[2, 4], help="difference order of --only fd")
     ap.add_argument("--suite", default=None, help="comma-separated grid sizes: run the Eqs. 9-21 expression suite")
     return ap.parse_args()
 
@@ -397,8 +398,9 @@ def extras(dev, stream, steps, x64, hbm):
 
 
 def only_form(args):
-    """One form alone, for profilers: forward (--variant), adjoint (binary64, loss W dtg + V Gamma) or
-    batched (--grids subgrids of the multi-domain recipe)."""
+    """One form alone, for profilers: forward (--variant), adjoint (loss W dtg + V Gamma), batched
+    (--grids subgrids of the multi-domain recipe), fd (derivatives on a periodic cube of about --n
+    points, --order) or generated (the chain program through the runtime generator)."""
     import torch
     import gridgen
     import paper_1804_10120_gb300 as tl
@@ -422,6 +424,22 @@ def only_form(args):
         g = torch.empty((43, n), dtype=torch.float64, device=dev)
         adj_dtype = "f64_ff" if args.variant == "f64_ff" else "f64"
         fn = lambda: tl.tl_dtg_backward(x, gout, g, dtype=adj_dtype, stream=stream)
+        units = n
+    elif args.only == "fd":
+        side = round(n ** (1.0 / 3.0))
+        shape = (side, side, side)
+        f = torch.from_numpy(gridgen.periodic_fields(shape, 1)).to(dev)
+        y = torch.empty((39, side ** 3), dtype=torch.float64, device=dev)
+        h = tuple(1.0 / m for m in shape)
+        fd_dtype = "f64_ff" if args.variant == "f64_ff" else "f64"
+        fn = lambda: tl.tl_dtg_forward_fd(f, shape, h, args.order, y, dtype=fd_dtype, stream=stream)
+        units = side ** 3
+    elif args.only == "generated":
+        from tests.jit_programs import PROGRAMS
+        x = torch.from_numpy(gridgen.random_grid(n, 1)).to(dev)
+        y = torch.empty((39, n), dtype=torch.float64, device=dev)
+        k = tl.JitKernel(PROGRAMS["chain"])
+        fn = lambda: k.launch(x, y, stream=stream)
         units = n
     else:
         sides = gridgen.subgrid_sides(args.grids, 2)
