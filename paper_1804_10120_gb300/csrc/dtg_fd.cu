@@ -25,6 +25,11 @@ struct FdArgs {
     double c1[3], c2[3];   // per axis: 1/(2h) (order 2) or 8/(12h), 1/(12h) (order 4)
 };
 
+// With equal spacings along the three axes every derivative is c1 times a plain difference,
+//   order 2:  f(x+h) - f(x-h),      order 4:  (f(x+h) - f(x-h)) - (f(x+2h) - f(x-2h)) / 8,
+// (8/12 = c1 h and 1/12 = c1 h / 8), so the kernel forms the differences and the chain applies c1 once
+// (to 1/2 g^il and inside nabla_j beta_i): 21 fewer binary64 operations per point.
+
 // Coordinate of the neighbour at offset o (|o| <= 2) along a periodic axis of length m: (i + o) mod m.
 // One conditional correction suffices when m >= 3; shorter axes take the modulo.
 __device__ __forceinline__ int wrapc(int i, int o, int m)
@@ -41,18 +46,18 @@ struct RowNeighbours {
     int64_t y[4], z[4];
 };
 
-template <int ORDER>
+template <int ORDER, bool UNIFORM>
 __device__ __forceinline__ double fd_axis(const double *__restrict__ f, int64_t x, const int64_t (&off)[4], double c1,
                                           double c2)
 {
     const double d1 = __ldg(f + x + off[2]) - __ldg(f + x + off[1]);
     if (ORDER == 2)
-        return d1 * c1;
+        return UNIFORM ? d1 : d1 * c1;
     const double d2 = __ldg(f + x + off[3]) - __ldg(f + x + off[0]);
-    return fma(d1, c1, -(d2 * c2));
+    return UNIFORM ? fma(d2, -0.125, d1) : fma(d1, c1, -(d2 * c2));
 }
 
-template <int ORDER>
+template <int ORDER, bool UNIFORM>
 __device__ __forceinline__ void fd_inputs(const FdArgs &a, int64_t x, const int64_t (&xo)[4], const RowNeighbours &rn,
                                           double (&v)[N_IN])
 {
@@ -60,9 +65,9 @@ __device__ __forceinline__ void fd_inputs(const FdArgs &a, int64_t x, const int6
     for (int p = 0; p < 6; ++p) {
         const double *f = a.in[FD_G + p];
         v[IN_G + p] = __ldg(f + x);
-        v[IN_DG + 3 * p + 0] = fd_axis<ORDER>(f, x, xo, a.c1[0], a.c2[0]);
-        v[IN_DG + 3 * p + 1] = fd_axis<ORDER>(f, x, rn.y, a.c1[1], a.c2[1]);
-        v[IN_DG + 3 * p + 2] = fd_axis<ORDER>(f, x, rn.z, a.c1[2], a.c2[2]);
+        v[IN_DG + 3 * p + 0] = fd_axis<ORDER, UNIFORM>(f, x, xo, a.c1[0], a.c2[0]);
+        v[IN_DG + 3 * p + 1] = fd_axis<ORDER, UNIFORM>(f, x, rn.y, a.c1[1], a.c2[1]);
+        v[IN_DG + 3 * p + 2] = fd_axis<ORDER, UNIFORM>(f, x, rn.z, a.c1[2], a.c2[2]);
         v[IN_K + p] = ld_stream(a.in[FD_K + p] + x);
     }
     v[IN_ALPHA] = ld_stream(a.in[FD_ALPHA] + x);
@@ -70,15 +75,15 @@ __device__ __forceinline__ void fd_inputs(const FdArgs &a, int64_t x, const int6
     for (int i = 0; i < 3; ++i) {
         const double *f = a.in[FD_BETA + i];
         v[IN_BETA + i] = __ldg(f + x);
-        v[IN_DBETA + 3 * i + 0] = fd_axis<ORDER>(f, x, xo, a.c1[0], a.c2[0]);
-        v[IN_DBETA + 3 * i + 1] = fd_axis<ORDER>(f, x, rn.y, a.c1[1], a.c2[1]);
-        v[IN_DBETA + 3 * i + 2] = fd_axis<ORDER>(f, x, rn.z, a.c1[2], a.c2[2]);
+        v[IN_DBETA + 3 * i + 0] = fd_axis<ORDER, UNIFORM>(f, x, xo, a.c1[0], a.c2[0]);
+        v[IN_DBETA + 3 * i + 1] = fd_axis<ORDER, UNIFORM>(f, x, rn.y, a.c1[1], a.c2[1]);
+        v[IN_DBETA + 3 * i + 2] = fd_axis<ORDER, UNIFORM>(f, x, rn.z, a.c1[2], a.c2[2]);
     }
 }
 
 // Blocks walk grid rows (iy, iz); the threads of a block walk the row's points.  All coordinate
 // arithmetic is per row except the x wrap.
-template <int ORDER, bool FF>
+template <int ORDER, bool FF, bool UNIFORM>
 __global__ void __launch_bounds__(256, 2) dtg_fd_kernel(const FdArgs a, int64_t n)
 {
     (void)n;
@@ -101,23 +106,29 @@ __global__ void __launch_bounds__(256, 2) dtg_fd_kernel(const FdArgs a, int64_t 
                 xo[q] = wrapc(ix, offs[q], nx) - ix;
             const int64_t x = row + ix;
             double v[N_IN];
-            fd_inputs<ORDER>(a, x, xo, rn, v);
-            if (!FF || !chain_ff(v, a, x))
-                chain_f64(v, a, x);
+            fd_inputs<ORDER, UNIFORM>(a, x, xo, rn, v);
+            if (!FF || !chain_ff<FdArgs, UNIFORM>(v, a, x, a.c1[0]))
+                chain_f64<FdArgs, UNIFORM>(v, a, x, a.c1[0]);
         }
     }
 }
 
-template <int ORDER, bool FF> static cudaError_t fd_launch(const FdArgs &a, int64_t n, int sms, cudaStream_t s)
+template <int ORDER, bool FF, bool UNIFORM>
+static cudaError_t fd_launch(const FdArgs &a, int64_t n, int sms, cudaStream_t s)
 {
     int blocks = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, dtg_fd_kernel<ORDER, FF>, 256, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, dtg_fd_kernel<ORDER, FF, UNIFORM>, 256, 0);
     if (e != cudaSuccess)
         return e;
     const int64_t rows = a.ny * a.nz;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(rows, (int64_t)sms * std::max(blocks, 1)));
-    dtg_fd_kernel<ORDER, FF><<<grid, 256, 0, s>>>(a, n);
+    dtg_fd_kernel<ORDER, FF, UNIFORM><<<grid, 256, 0, s>>>(a, n);
     return cudaGetLastError();
+}
+
+template <int ORDER, bool FF> static cudaError_t fd_launch(const FdArgs &a, int64_t n, int sms, cudaStream_t s, bool uniform)
+{
+    return uniform ? fd_launch<ORDER, FF, true>(a, n, sms, s) : fd_launch<ORDER, FF, false>(a, n, sms, s);
 }
 
 }  // namespace tl
@@ -170,8 +181,10 @@ extern "C" tl_status tl_dtg_forward_fd(const tl_dtg_grid_in *in, const tl_dtg_ou
     }
     const cudaStream_t st = (cudaStream_t)stream;
     const bool ff = dtype == TL_F64_FF;
-    cudaError_t e = grid->order == 2 ? (ff ? fd_launch<2, true>(a, n, d->sms, st) : fd_launch<2, false>(a, n, d->sms, st))
-                                     : (ff ? fd_launch<4, true>(a, n, d->sms, st) : fd_launch<4, false>(a, n, d->sms, st));
+    const bool u = grid->hx == grid->hy && grid->hy == grid->hz;
+    cudaError_t e = grid->order == 2
+                        ? (ff ? fd_launch<2, true>(a, n, d->sms, st, u) : fd_launch<2, false>(a, n, d->sms, st, u))
+                        : (ff ? fd_launch<4, true>(a, n, d->sms, st, u) : fd_launch<4, false>(a, n, d->sms, st, u));
     if (e != cudaSuccess)
         return cuda_fail(e, "on-grid forward launch");
     return TL_OK;

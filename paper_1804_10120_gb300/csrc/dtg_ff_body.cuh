@@ -8,9 +8,10 @@ namespace tl {
 
 // The chain on one point's 43 input values (in registers, input-table order), outputs to o.out[s][x].
 // Returns false, having stored nothing but g^ij, when a value falls outside the pair format's range;
-// the caller then evaluates the point in binary64.
-template <class OutTable>
-__device__ __forceinline__ bool chain_ff(const double (&v)[N_IN], const OutTable &o, int64_t x)
+// the caller then evaluates the point in binary64.  kScaled and sd as for chain_f64: the 27 derivative
+// entries are differences still to be multiplied by sd.
+template <class OutTable, bool kScaled = false>
+__device__ __forceinline__ bool chain_ff(const double (&v)[N_IN], const OutTable &o, int64_t x, double sd = 1.0)
 {
     const double g00 = v[IN_G + 0], g01 = v[IN_G + 1],
                  g02 = v[IN_G + 2], g11 = v[IN_G + 3],
@@ -36,7 +37,10 @@ __device__ __forceinline__ bool chain_ff(const double (&v)[N_IN], const OutTable
     for (int p = 0; p < 6; ++p) {
         const double gi = c[p] * rdet;
         st_stream(o.out[OUT_GINV + p] + x, gi);
-        h[p] = split_ff(half_exact(gi), big);
+        if constexpr (kScaled)
+            h[p] = split_ff(gi * half_exact(sd), big);
+        else
+            h[p] = split_ff(half_exact(gi), big);
     }
 
     // bracket of Eq. 6 in binary64, then pairs
@@ -77,7 +81,10 @@ __device__ __forceinline__ bool chain_ff(const double (&v)[N_IN], const OutTable
     for (int i = 0; i < 3; ++i)
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
-            nb[i][j] = v[IN_DBETA + 3 * i + j] - S6[sym(i, j)];
+            if constexpr (kScaled)
+                nb[i][j] = fma(sd, v[IN_DBETA + 3 * i + j], -S6[sym(i, j)]);
+            else
+                nb[i][j] = v[IN_DBETA + 3 * i + j] - S6[sym(i, j)];
             st_stream(o.out[OUT_DBCOV + 3 * i + j] + x, nb[i][j]);
         }
 

@@ -40,9 +40,12 @@ __device__ __forceinline__ void christoffel_bracket(const R (&dg)[18], R (&T)[3]
 
 // ------------------------------------------------------------------------------------ binary64 forward
 // The chain on one point's 43 input values (already in registers, in the input-table order); the 39
-// outputs go to o.out[s][x] (o: any argument block with an `out` table).
-template <class OutTable>
-__device__ __forceinline__ void chain_f64(const double (&v)[N_IN], const OutTable &o, int64_t x)
+// outputs go to o.out[s][x] (o: any argument block with an `out` table).  kScaled: the d_k g_ij and
+// d_j beta_i entries of v are differences that still need one common factor sd (a finite-difference
+// stencil on a grid with equal spacings); sd is then applied once to 1/2 g^il and fused into
+// nabla_j beta_i instead of to each of the 27 derivatives.
+template <class OutTable, bool kScaled = false>
+__device__ __forceinline__ void chain_f64(const double (&v)[N_IN], const OutTable &o, int64_t x, double sd = 1.0)
 {
     // step 1: inverse metric by cofactors; det by first-row expansion
     const double g00 = v[IN_G + 0], g01 = v[IN_G + 1],
@@ -66,7 +69,10 @@ __device__ __forceinline__ void chain_f64(const double (&v)[N_IN], const OutTabl
 #pragma unroll
     for (int p = 0; p < 6; ++p) {
         ginv[p] = c[p] * rdet;
-        h[p] = half_exact(ginv[p]);          // 1/2 g^il of Eq. 6
+        if constexpr (kScaled)
+            h[p] = ginv[p] * half_exact(sd);
+        else
+            h[p] = half_exact(ginv[p]);      // 1/2 g^il of Eq. 6
         st_stream(o.out[OUT_GINV + p] + x, ginv[p]);
     }
 
@@ -85,14 +91,22 @@ __device__ __forceinline__ void chain_f64(const double (&v)[N_IN], const OutTabl
     // step 3: nabla_j beta_i = d_j beta_i - Gamma^k_ij beta_k
     const double b0 = v[IN_BETA + 0], b1 = v[IN_BETA + 1],
                  b2 = v[IN_BETA + 2];
-    double nb[3][3];
+    double nb[3][3], S6[6];
+    if constexpr (kScaled) {
+#pragma unroll
+        for (int p = 0; p < 6; ++p)           // Gamma^k_ij beta_k is symmetric in ij: 6 sums
+            S6[p] = fma(gam[2][p], b2, fma(gam[1][p], b1, gam[0][p] * b0));
+    }
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
             const int p = sym(i, j);
             const double B = v[IN_DBETA + 3 * i + j];
-            nb[i][j] = fma(-gam[2][p], b2, fma(-gam[1][p], b1, fma(-gam[0][p], b0, B)));
+            if constexpr (kScaled)
+                nb[i][j] = fma(sd, B, -S6[p]);
+            else
+                nb[i][j] = fma(-gam[2][p], b2, fma(-gam[1][p], b1, fma(-gam[0][p], b0, B)));
             st_stream(o.out[OUT_DBCOV + 3 * i + j] + x, nb[i][j]);
         }
 

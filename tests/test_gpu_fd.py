@@ -11,10 +11,10 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
-def run(shape, order, dtype, seed=5):
+def run(shape, order, dtype, seed=5, h=None):
     import paper_1804_10120_gb300 as tl
     f = gridgen.periodic_fields(shape, seed)
-    h = tuple(1.0 / m for m in shape)
+    h = h or tuple(1.0 / m for m in shape)
     y = tl.tl_dtg_forward_fd(torch.from_numpy(f).to(torch.device("cuda", 0)), shape, h, order, dtype=dtype)
     torch.cuda.synchronize()
     return f, h, y
@@ -23,10 +23,13 @@ def run(shape, order, dtype, seed=5):
 @pytest.mark.parametrize("dtype", ["f64", "f64_ff"])
 @pytest.mark.parametrize("order", [2, 4])
 @pytest.mark.parametrize("shape", [(16, 12, 10), (1, 1, 9), (3, 2, 1), (37, 5, 7)])
-def test_fd_forward_matches_oracle(shape, order, dtype):
-    f, h, y = run(shape, order, dtype)
+@pytest.mark.parametrize("spacing", ["per_axis", "equal"])
+def test_fd_forward_matches_oracle(shape, order, dtype, spacing):
+    """Spacings 1/n_axis (unequal: each derivative scaled in the stencil) and 0.07 on every axis
+    (equal: the kernel forms plain differences and the chain applies the common factor once)."""
+    f, h, y = run(shape, order, dtype, h=(0.07, 0.07, 0.07) if spacing == "equal" else None)
     ref = oracle.forward(oracle.fd_inputs(f, shape, h, order))
-    assert_components(y.cpu().numpy(), ref, TOL_F64, what="fd %s order %d %s" % (shape, order, dtype))
+    assert_components(y.cpu().numpy(), ref, TOL_F64, what="fd %s order %d %s %s" % (shape, order, dtype, spacing))
 
 
 def test_fd_forward_full_grid_sampled():
