@@ -65,10 +65,12 @@ _COMMON = ["tl_common.cuh", "tl_kernels.h"]
 KERNEL_SOURCES = {
     "dtg_fwd_f64_kernel": ["dtg_fwd.cu", "dtg_fwd_body.cuh", "dtg_batched.cuh"] + _COMMON,
     "dtg_fwd_f32_kernel": ["dtg_fwd.cu", "dtg_fwd_body.cuh", "dtg_batched.cuh"] + _COMMON,
-    "dtg_fwd_ff_kernel": ["dtg_fwd_ff.cu", "dtg_fwd_body.cuh", "ff.cuh", "dtg_batched.cuh"] + _COMMON,
+    "dtg_fwd_ff_kernel": ["dtg_fwd_ff.cu", "dtg_fwd_body.cuh", "dtg_ff_body.cuh", "ff.cuh", "dtg_batched.cuh"] + _COMMON,
     "dtg_bwd_f64_kernel": ["dtg_bwd.cu", "dtg_fwd_body.cuh", "ff.cuh"] + _COMMON,
     "dtg_bwd_ff_kernel": ["dtg_bwd.cu", "dtg_fwd_body.cuh", "ff.cuh"] + _COMMON,
     "dtg_batched_f64_kernel": ["dtg_fwd.cu", "dtg_fwd_body.cuh", "dtg_batched.cuh"] + _COMMON,
+    "dtg_fd_kernel": ["dtg_fd.cu", "dtg_fwd_body.cuh", "dtg_ff_body.cuh", "ff.cuh"] + _COMMON,
+    "tl_jit_kernel": ["jit.cu"],
 }
 
 
