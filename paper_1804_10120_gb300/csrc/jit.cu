@@ -777,14 +777,17 @@ void generate(Program &P)
     std::ostringstream src;
     src << "// generated from a tensor-index program; one thread per grid point\n"
         << "// x * 2^k (|k| <= 8) by adjusting the exponent field with an integer add; zero, subnormal, huge,\n"
-        << "// inf and nan operands take the multiplication\n"
+        << "// inf and nan operands take the multiplication, out of line: inline, the compiler if-converts it\n"
+        << "// and every call then occupies an FP64 issue slot even with its predicate off\n"
+        << "__device__ __noinline__ double tl_pow2_slow(double x, int k)\n{\n"
+        << "  return x * __hiloint2double((1023 + k) << 20, 0);\n}\n"
         << "__device__ __forceinline__ double tl_pow2(double x, int k)\n{\n"
         << "  const int hi = __double2hiint(x), lo = __double2loint(x);\n"
         << "  const unsigned e = ((unsigned)hi >> 20) & 0x7ffu;\n"
         << "  if (e > 8u && e < 2047u - 8u) { int r; asm(\"add.s32 %0, %1, %2;\" : \"=r\"(r) : \"r\"(hi), \"r\"(k << 20));\n"
         << "    return __hiloint2double(r, lo); }\n"
         << "  if (((hi & 0x7fffffff) | lo) == 0) return x;\n"
-        << "  return x * __hiloint2double((1023 + k) << 20, 0);\n}\n"
+        << "  return tl_pow2_slow(x, k);\n}\n"
         << "struct TlJitArgs { const double *in[" << std::max(P.n_in, 1) << "]; double *out[" << P.n_out << "]; };\n"
         << "extern \"C\" __global__ void __launch_bounds__(256) tl_jit_kernel(const TlJitArgs a, long long n)\n{\n"
         << "  for (long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x; x < n;\n"
