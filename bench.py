@@ -28,7 +28,7 @@ METRIC = "grid points/s and HBM GB/s, fused Christoffel+dt g_ij, fwd and fwd+adj
 UNIT = "grid points/s"
 N_FULL = 1 << 24
 BYTES_PER_POINT = {"f64": 656, "f64_ff": 656, "f32": 328}
-KERNEL_NAME = {"f64": "dtg_fwd_f64_kernel", "f64_ff": "dtg_fwd_ff_kernel", "f32": "dtg_fwd_f32_kernel"}
+KERNEL_NAME = {"f64": "dtg_fwd_f64_kernel", "f64_ff": "dtg_fwd_ff_kernel", "f32": "dtg_fwd_f32_staged_kernel"}
 
 
 def parse():
@@ -65,6 +65,7 @@ _COMMON = ["tl_common.cuh", "tl_kernels.h"]
 KERNEL_SOURCES = {
     "dtg_fwd_f64_kernel": ["dtg_fwd.cu", "dtg_fwd_body.cuh", "dtg_batched.cuh"] + _COMMON,
     "dtg_fwd_f32_kernel": ["dtg_fwd.cu", "dtg_fwd_body.cuh", "dtg_batched.cuh"] + _COMMON,
+    "dtg_fwd_f32_staged_kernel": ["dtg_fwd.cu", "dtg_fwd_body.cuh", "dtg_batched.cuh", "bulk.cuh"] + _COMMON,
     "dtg_fwd_ff_kernel": ["dtg_fwd_ff.cu", "dtg_fwd_body.cuh", "dtg_ff_body.cuh", "ff.cuh", "dtg_batched.cuh"] + _COMMON,
     "dtg_bwd_f64_kernel": ["dtg_bwd.cu", "dtg_fwd_body.cuh", "ff.cuh"] + _COMMON,
     "dtg_bwd_ff_kernel": ["dtg_bwd.cu", "dtg_fwd_body.cuh", "ff.cuh"] + _COMMON,

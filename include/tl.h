@@ -228,6 +228,15 @@ typedef struct { int64_t nx, ny, nz; double hx, hy, hz; int32_t order; } tl_grid
 TL_API tl_status tl_dtg_forward_fd(const tl_dtg_grid_in *in, const tl_dtg_out *out, const tl_grid3d *grid,
                                    tl_dtype dtype, tl_stream stream);
 
+/*
+ * Kernels that stage inputs through shared memory (the TL_F32 forward) wait on their own bulk copies
+ * with a bounded number of polls; a wait that gives up makes its block stop early and counts here,
+ * so a nonzero count means some outputs of an earlier call were not written.  *count = timeouts on
+ * the current device since the library was loaded.  Synchronises with the device (host call only,
+ * not capturable); TL_ERR_CUDA if the read fails.  Expected to stay 0.
+ */
+TL_API tl_status tl_wait_timeouts(uint32_t *count);
+
 TL_API const char *tl_status_string(tl_status s);
 TL_API const char *tl_last_error(void);
 /* Library version as MAJOR*10000 + MINOR*100 + PATCH. */

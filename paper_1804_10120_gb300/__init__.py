@@ -172,6 +172,17 @@ def tl_dtg_backward(inputs, gout, gin=None, dtype="f64", stream=None):
     return gin
 
 
+def tl_wait_timeouts():
+    """Bounded device waits that gave up on the current device since the library was loaded (0 unless
+    a staged kernel stopped early; synchronises)."""
+    L = lib()
+    L.tl_wait_timeouts.argtypes = [ctypes.c_void_p]
+    L.tl_wait_timeouts.restype = ctypes.c_int
+    c = ctypes.c_uint32()
+    _check(L.tl_wait_timeouts(ctypes.byref(c)))
+    return c.value
+
+
 def tl_dtg_host_workspace_bytes(n, dtype="f64"):
     return int(lib().tl_dtg_host_workspace_bytes(n, _dtype_code(dtype)))
 

@@ -7,6 +7,9 @@
 // kernels (one thread per point and output component, one kernel per expression, pointer tables
 // read from global memory; Sec. 4), the whole chain is one kernel and the pointer tables are kernel
 // parameters.
+#include <algorithm>
+
+#include "bulk.cuh"
 #include "dtg_batched.cuh"
 #include "dtg_fwd_body.cuh"
 
@@ -33,17 +36,13 @@ __device__ __forceinline__ float narrow(double d, uint32_t &rare)
     return kIntConv ? f64_to_f32(d, rare) : (float)d;
 }
 
-// kIntConv: binary32 <-> binary64 conversions on the integer pipe (returns false, having written nothing,
-// when an operand needs the general conversions); otherwise the compiler's F2F conversions.
+// The chain on one point's 43 binary32 inputs (in registers, input-table order), outputs to
+// a.out[s][x].  kIntConv: binary32 <-> binary64 conversions on the integer pipe (returns false, having
+// written nothing, when an operand needs the general conversions); otherwise the compiler's F2F
+// conversions.
 template <bool kIntConv>
-__device__ __forceinline__ bool fwd_point_f32(const FwdArgs<float> &a, int64_t x)
+__device__ __forceinline__ bool chain_f32(const float (&v)[N_IN], const FwdArgs<float> &a, int64_t x)
 {
-    float v[N_IN];
-#pragma unroll
-    for (int s = 0; s < N_IN; ++s)
-        v[s] = ld_stream(a.in[s] + x);
-    asm volatile("" ::: "memory");   // every load is issued before any arithmetic
-
     // step 1 in binary64 from the exactly widened metric; g^ij rounded once to binary32
     uint32_t rare = 0;
     const double g00 = widen<kIntConv>(v[IN_G + 0], rare), g01 = widen<kIntConv>(v[IN_G + 1], rare),
@@ -111,6 +110,17 @@ __device__ __forceinline__ bool fwd_point_f32(const FwdArgs<float> &a, int64_t x
     return true;
 }
 
+template <bool kIntConv>
+__device__ __forceinline__ bool fwd_point_f32(const FwdArgs<float> &a, int64_t x)
+{
+    float v[N_IN];
+#pragma unroll
+    for (int s = 0; s < N_IN; ++s)
+        v[s] = ld_stream(a.in[s] + x);
+    asm volatile("" ::: "memory");   // every load is issued before any arithmetic
+    return chain_f32<kIntConv>(v, a, x);
+}
+
 // The general-conversion evaluation of one point, out of line (rare operands only).
 __device__ __noinline__ void fwd_point_f32_general(const FwdArgs<float> &a, int64_t x) { fwd_point_f32<false>(a, x); }
 
@@ -120,6 +130,94 @@ __global__ void __launch_bounds__(kFwdThreads) dtg_fwd_f32_kernel(const FwdArgs<
     for (int64_t x = gs.first; x < n; x += gs.step)
         if (!fwd_point_f32<true>(a, x))
             fwd_point_f32_general(a, x);
+}
+
+// ------------------------------------------------------------------- binary32 forward, staged inputs
+// The binary32 form moves 328 bytes per point against 24 FP64 operations, so it is bound by how many
+// loads are in flight rather than by arithmetic.  Here the 43 input streams of a tile of TILE points
+// are brought into shared memory by the bulk-copy engine, STAGES tiles ahead of the threads that
+// compute on them: one thread issues 43 copies of TILE * 4 contiguous bytes per tile, completion is
+// counted in bytes on one mbarrier per stage, and the loads overlap the arithmetic of earlier tiles.
+// 512 points x 2 stages (176 KB: one block, 16 warps per SM) measured best, 0.96 ms at N = 2^24
+// against 1.00 ms for the plain kernel; 256 x 4 and 384 x 3 (8 and 12 warps) leave the binary64
+// inverse latency-bound, and 640 x 2 or 768 x 2 (K and alpha then read directly) were slower.
+// Each block walks tiles blockIdx.x, + gridDim.x, ...
+// One __syncthreads per tile (after the wait) certifies that every thread has finished the previous
+// tile, whose stage is then refilled.  Requires 16-byte aligned input streams; the last n % TILE
+// points are left to the plain kernel.
+__device__ unsigned int g_wait_timeouts;   // waits that gave up (a bulk copy never completed)
+
+constexpr uint32_t kWaitPolls = 1u << 18;
+
+template <int TILE, int STAGES>
+__global__ void __launch_bounds__(TILE) dtg_fwd_f32_staged_kernel(const FwdArgs<float> a, int64_t ntiles)
+{
+    extern __shared__ __align__(128) float stage_buf[];   // [STAGES][N_IN][TILE]
+    __shared__ __align__(8) uint64_t full[STAGES];
+    const int tid = threadIdx.x;
+    const int64_t count = ntiles > (int64_t)blockIdx.x ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    if (tid == 0) {
+#pragma unroll
+        for (int s = 0; s < STAGES; ++s)
+            mbar_init(&full[s], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    auto issue = [&](int64_t i) {   // thread 0: the block's tile i into stage i % STAGES
+        const int s = (int)(i % STAGES);
+        const int64_t t = (int64_t)blockIdx.x + i * gridDim.x;
+        float *dst = stage_buf + (size_t)s * N_IN * TILE;
+        mbar_arrive_expect_tx(&full[s], N_IN * TILE * (uint32_t)sizeof(float));
+#pragma unroll 1
+        for (int k = 0; k < N_IN; ++k)
+            bulk_copy_g2s(dst + k * TILE, a.in[k] + t * TILE, TILE * (uint32_t)sizeof(float), &full[s]);
+    };
+    if (tid == 0)
+        for (int64_t i = 0; i < STAGES - 1 && i < count; ++i)
+            issue(i);
+    for (int64_t i = 0; i < count; ++i) {
+        const int s = (int)(i % STAGES);
+        const bool ok = mbar_wait(&full[s], (uint32_t)((i / STAGES) & 1), kWaitPolls);
+        if (__syncthreads_or(!ok)) {   // block-uniform: record, let issued copies land, leave
+            if (tid == 0) {
+                atomicAdd(&g_wait_timeouts, 1u);
+                for (int64_t j = i; j < count && j < i + STAGES - 1; ++j)
+                    mbar_wait(&full[j % STAGES], (uint32_t)((j / STAGES) & 1), kWaitPolls);
+            }
+            return;
+        }
+        if (tid == 0 && i + STAGES - 1 < count)
+            issue(i + STAGES - 1);
+        const float *src = stage_buf + (size_t)s * N_IN * TILE + tid;
+        float v[N_IN];
+#pragma unroll
+        for (int k = 0; k < N_IN; ++k)
+            v[k] = src[k * TILE];
+        const int64_t x = ((int64_t)blockIdx.x + i * gridDim.x) * TILE + tid;
+        if (!chain_f32<true>(v, a, x))
+            fwd_point_f32_general(a, x);
+    }
+}
+
+template <int TILE, int STAGES>
+static cudaError_t launch_f32_staged(const FwdArgs<float> &a, int64_t ntiles, int sms, cudaStream_t s)
+{
+    const size_t smem = (size_t)STAGES * N_IN * TILE * sizeof(float);
+    auto kern = dtg_fwd_f32_staged_kernel<TILE, STAGES>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int blocks = 0;
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, TILE, smem);
+    if (e != cudaSuccess)
+        return e;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)sms * std::max(blocks, 1)));
+    kern<<<grid, TILE, smem, s>>>(a, ntiles);
+    return cudaGetLastError();
+}
+
+cudaError_t read_wait_timeouts(unsigned int *count)
+{
+    return cudaMemcpyFromSymbol(count, g_wait_timeouts, sizeof(unsigned int));
 }
 
 // ------------------------------------------------------------------------------------ batched forward
@@ -187,6 +285,27 @@ cudaError_t launch_fwd_f32(const FwdArgs<float> &a, int64_t n, int grid, cudaStr
 {
     dtg_fwd_f32_kernel<<<grid, kFwdThreads, 0, s>>>(a, n);
     return cudaGetLastError();
+}
+
+cudaError_t launch_fwd_f32_staged(const FwdArgs<float> &a, int64_t n, int sms, int tail_grid, cudaStream_t s)
+{
+    constexpr int kTile = kF32StagedTile;
+    bool aligned = true;
+    for (int k = 0; k < N_IN; ++k)
+        aligned = aligned && ((uintptr_t)a.in[k] % 16 == 0);
+    const int64_t ntiles = aligned ? n / kTile : 0;
+    cudaError_t e = cudaSuccess;
+    if (ntiles > 0)
+        e = launch_f32_staged<kTile, kF32StagedStages>(a, ntiles, sms, s);
+    const int64_t done = ntiles * kTile;
+    if (e != cudaSuccess || done == n)
+        return e;
+    FwdArgs<float> t = a;   // the remaining points: plain kernel on the shifted tables
+    for (int k = 0; k < N_IN; ++k)
+        t.in[k] += done;
+    for (int k = 0; k < N_OUT; ++k)
+        t.out[k] += done;
+    return launch_fwd_f32(t, n - done, (int)std::min<int64_t>(tail_grid, (n - done + kFwdThreads - 1) / kFwdThreads), s);
 }
 
 cudaError_t occupancy_fwd(int *f64, int *f32, int *ff)

@@ -165,7 +165,8 @@ tl_status launch_forward(const DeviceInfo &d, const tl_dtg_in *in, const tl_dtg_
         e = launch_fwd_f64(fwd_args<double>(in, out), n, grid_for(n, kFwdThreads, d.sms, d.fwd_f64_blocks), st);
         break;
     case TL_F32:
-        e = launch_fwd_f32(fwd_args<float>(in, out), n, grid_for(n, kFwdThreads, d.sms, d.fwd_f32_blocks), st);
+        e = launch_fwd_f32_staged(fwd_args<float>(in, out), n, d.sms, grid_for(n, kFwdThreads, d.sms, d.fwd_f32_blocks),
+                                  st);
         break;
     case TL_F64_FF:
         e = launch_fwd_ff(fwd_args<double>(in, out), n, grid_for(n, kFwdThreads, d.sms, d.fwd_ff_blocks), st);
@@ -303,6 +304,22 @@ const char *tl_status_string(tl_status s)
 const char *tl_last_error(void) { return g_last_error.c_str(); }
 
 int tl_version(void) { return 10000; }
+
+tl_status tl_wait_timeouts(uint32_t *count)
+{
+    if (!count)
+        return fail(TL_ERR_INVALID_ARG, "NULL count");
+    const DeviceInfo *d = nullptr;
+    tl_status s = device_info(&d);
+    if (s != TL_OK)
+        return s;
+    unsigned int c = 0;
+    cudaError_t e = read_wait_timeouts(&c);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "reading the wait-timeout counter");
+    *count = c;
+    return TL_OK;
+}
 
 tl_status tl_dtg_forward(const tl_dtg_in *in, const tl_dtg_out *out, int64_t n, tl_dtype dtype, tl_stream stream)
 {

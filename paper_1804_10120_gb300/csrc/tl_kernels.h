@@ -12,6 +12,14 @@ constexpr int kBwdThreads = 128;
 
 cudaError_t launch_fwd_f64(const FwdArgs<double> &a, int64_t n, int grid, cudaStream_t s);
 cudaError_t launch_fwd_f32(const FwdArgs<float> &a, int64_t n, int grid, cudaStream_t s);
+// Binary32 forward with the inputs staged through shared memory by bulk copies (tiles of
+// kF32StagedTile points, kF32StagedStages deep); falls back to launch_fwd_f32 (grid tail_grid) for
+// unaligned inputs and for the last n % kF32StagedTile points.
+constexpr int kF32StagedTile = 512;
+constexpr int kF32StagedStages = 2;
+cudaError_t launch_fwd_f32_staged(const FwdArgs<float> &a, int64_t n, int sms, int tail_grid, cudaStream_t s);
+// Number of bounded waits in the staged kernels that gave up since the library was loaded.
+cudaError_t read_wait_timeouts(unsigned int *count);
 cudaError_t launch_fwd_ff(const FwdArgs<double> &a, int64_t n, int grid, cudaStream_t s);
 cudaError_t launch_bwd_f64(const BwdArgs<double> &a, int64_t n, int grid, cudaStream_t s);
 cudaError_t launch_bwd_ff(const BwdArgs<double> &a, int64_t n, int grid, cudaStream_t s);

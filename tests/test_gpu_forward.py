@@ -257,3 +257,30 @@ def test_f32_rare_operands_take_general_conversions():
     torch.cuda.synchronize()
     err = component_errors(y.cpu().numpy().astype(np.float64), oracle.forward(x.astype(np.float64)))
     assert err.max() <= TOL_F32_COMPUTE
+
+
+@pytest.mark.parametrize("n", [1, 255, 256, 257, 4099, 3 * 256 * 152 + 77])
+def test_f32_staged_equals_plain_kernel_bitwise(n):
+    """16-byte aligned input tables take the shared-memory-staged kernel (tiles of 256 points, the
+    last n % 256 points by the plain kernel); the same inputs one element off alignment take the plain
+    kernel alone.  Both evaluate the same binary32 chain, so the outputs agree bit for bit, and they
+    meet the oracle bound; no bounded wait gives up."""
+    import paper_1804_10120_gb300 as tl
+    x = gridgen.random_grid(n, 44).astype(np.float32)
+    npad = (n + 3) // 4 * 4                       # rows start on 16-byte boundaries
+    abuf = torch.zeros((43, npad), dtype=torch.float32, device=dev())
+    abuf[:, :n] = torch.from_numpy(x).to(dev())
+    xa = [abuf[k, :n] for k in range(43)]
+    assert all(r.data_ptr() % 16 == 0 for r in xa)
+    buf = torch.empty((43, n + 1), dtype=torch.float32, device=dev())
+    buf[:, 1:] = abuf[:, :n]
+    xu = buf[:, 1:]
+    assert xu[0].data_ptr() % 16 != 0
+    ya = tl.tl_dtg_forward(xa, dtype="f32")
+    yu = tl.tl_dtg_forward([xu[k] for k in range(43)], dtype="f32")
+    torch.cuda.synchronize()
+    assert torch.equal(ya, yu)
+    idx = np.unique(np.linspace(0, n - 1, min(n, 3000)).astype(np.int64))
+    err = component_errors(ya.cpu().numpy()[:, idx].astype(np.float64), oracle.forward(x[:, idx].astype(np.float64)))
+    assert err.max() <= TOL_F32_COMPUTE
+    assert tl.tl_wait_timeouts() == 0
