@@ -367,8 +367,8 @@ def extras(dev, stream, steps, x64, hbm):
                 "bytes_per_point": "16 arrays read + 39 written = 440"}
     del fd_fields, y
     # the same chain written as a tensor-index program, emitted and compiled at run time
-    from tests.jit_programs import PROGRAMS
-    k = tl.JitKernel(PROGRAMS["chain"])
+    from paper_1804_10120_gb300.programs import CHAIN
+    k = tl.JitKernel(CHAIN)
     y = torch.empty((39, n), dtype=torch.float64, device=dev)
     ms_gen = cuda_time(lambda: k.launch(x64, y, stream=stream), steps, stream)
     out["generated_chain"] = {"workload": "single grid N=2^24, seed 1; the chain as a 16-statement index program "
@@ -380,7 +380,7 @@ def extras(dev, stream, steps, x64, hbm):
     # intermediates through device memory (the paper's evaluation model and its "Arrays" baseline)
     from paper_1804_10120_gb300.statements import StatementPipeline
     for mode in ("statement", "component"):
-        pl = StatementPipeline(PROGRAMS["chain"], mode)
+        pl = StatementPipeline(CHAIN, mode)
         ms_st = cuda_time(lambda: pl.run(x64, y, stream=stream), steps, stream)
         elems = pl.elements_per_point()
         out["generated_chain"]["per_" + mode] = {
@@ -438,10 +438,10 @@ def only_form(args):
         fn = lambda: tl.tl_dtg_forward_fd(f, shape, h, args.order, y, dtype=fd_dtype, stream=stream)
         units = side ** 3
     elif args.only == "generated":
-        from tests.jit_programs import PROGRAMS
+        from paper_1804_10120_gb300.programs import CHAIN
         x = torch.from_numpy(gridgen.random_grid(n, 1)).to(dev)
         y = torch.empty((39, n), dtype=torch.float64, device=dev)
-        k = tl.JitKernel(PROGRAMS["chain"])
+        k = tl.JitKernel(CHAIN)
         fn = lambda: k.launch(x, y, stream=stream)
         units = n
     else:

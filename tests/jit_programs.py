@@ -1,5 +1,8 @@
-"""Tensor-index programs shared by the generator tests (plain text; no arithmetic here)."""
-from tests.test_tensor_expr_oracle import CHAIN, EXPR_PROGRAMS
+"""Tensor-index programs shared by the generator tests (plain text; no arithmetic here).  "chain" is
+the package's own program, the one the benchmark compiles; the interpreter pins check it against the
+chain oracle."""
+from paper_1804_10120_gb300.programs import CHAIN
+from tests.test_tensor_expr_oracle import EXPR_PROGRAMS
 
 PROGRAMS = {
     "chain": CHAIN,

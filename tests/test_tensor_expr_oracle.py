@@ -2,6 +2,7 @@
 evolution chain written as a program equals the chain oracle; the benchmark expressions equal their
 literal oracle bit for bit; the paper's two contraction listings equal numpy.einsum."""
 import numpy as np
+import pytest
 
 import gridgen
 import oracle
@@ -36,8 +37,10 @@ EXPR_PROGRAMS = {
 }
 
 
-def test_chain_program_equals_chain_oracle():
-    p = Program(CHAIN)
+@pytest.mark.parametrize("which", ["transcribed here", "shipped with the package"])
+def test_chain_program_equals_chain_oracle(which):
+    from paper_1804_10120_gb300.programs import CHAIN as PACKAGE_CHAIN
+    p = Program(CHAIN if which == "transcribed here" else PACKAGE_CHAIN)
     assert len(p.inputs()) == 43 and len(p.outputs()) == 39
     x = gridgen.random_grid(2000, 13)
     y = p.run(x)
