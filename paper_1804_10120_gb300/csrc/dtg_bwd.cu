@@ -139,11 +139,15 @@ template <bool kU, bool kG> __device__ __forceinline__ void bwd_point_f64(const 
         for (int p = 0; p < 6; ++p)
             Tb[l][p] = fma(h[sym(2, l)], gbar[2][p], fma(h[sym(1, l)], gbar[1][p], h[sym(0, l)] * gbar[0][p]));
 
-    // ---- bracket -> d_k g_ij: every T_lp term of Eq. 6 scattered onto the stored derivative it reads
+    // ---- bracket -> d_k g_ij: every T_lp term of Eq. 6 scattered onto the stored derivative it reads.
+    // The first contribution to an entry is assigned rather than added to zero (an FP64 add saved per
+    // entry; `seen` is resolved at compile time once the loops are unrolled).
     double dgb[18];
-#pragma unroll
-    for (int s = 0; s < 18; ++s)
-        dgb[s] = 0.0;
+    bool seen[18] = {};
+    auto put = [&](int s, double t) {
+        dgb[s] = seen[s] ? dgb[s] + t : t;
+        seen[s] = true;
+    };
 #pragma unroll
     for (int l = 0; l < 3; ++l)
 #pragma unroll
@@ -152,16 +156,16 @@ template <bool kU, bool kG> __device__ __forceinline__ void bwd_point_f64(const 
             for (int k = j; k < 3; ++k) {
                 const double t = Tb[l][sym(j, k)];
                 if (l == j) {                       // T = d_k g_jj
-                    dgb[3 * sym(j, j) + k] += t;
+                    put(3 * sym(j, j) + k, t);
                 } else if (l == k) {                // T = d_j g_kk
-                    dgb[3 * sym(k, k) + j] += t;
+                    put(3 * sym(k, k) + j, t);
                 } else if (j == k) {                // T = 2 d_j g_jl - d_l g_jj
-                    dgb[3 * sym(j, l) + j] += twice_exact(t);
-                    dgb[3 * sym(j, j) + l] -= t;
+                    put(3 * sym(j, l) + j, twice_exact(t));
+                    put(3 * sym(j, j) + l, -t);
                 } else {                            // T = d_k g_jl + d_j g_lk - d_l g_jk
-                    dgb[3 * sym(j, l) + k] += t;
-                    dgb[3 * sym(l, k) + j] += t;
-                    dgb[3 * sym(j, k) + l] -= t;
+                    put(3 * sym(j, l) + k, t);
+                    put(3 * sym(l, k) + j, t);
+                    put(3 * sym(j, k) + l, -t);
                 }
             }
 #pragma unroll
@@ -348,9 +352,14 @@ template <bool kU, bool kG> __device__ __forceinline__ void bwd_point_ff(const B
 
     // Tbar_lp = sum_i h_il Gammabar_ip, scattered through the bracket onto d_k g_ij
     ffacc D[18];
-#pragma unroll
-    for (int s = 0; s < 18; ++s)
-        D[s] = ffacc{0.0f, 0.0f};
+    bool seen[18] = {};
+    auto put = [&](int s, ff t) {   // first contribution assigned (resolved at compile time)
+        if (seen[s])
+            acc_add(D[s], t);
+        else
+            D[s] = acc_from(t);
+        seen[s] = true;
+    };
 #pragma unroll
     for (int l = 0; l < 3; ++l)
 #pragma unroll
@@ -363,16 +372,16 @@ template <bool kU, bool kG> __device__ __forceinline__ void bwd_point_ff(const B
                 acc_add_prod(A, hf[sym(2, l)], gb[2][p]);
                 const ff t = acc_result(A);
                 if (l == j) {
-                    acc_add(D[3 * sym(j, j) + k], t);
+                    put(3 * sym(j, j) + k, t);
                 } else if (l == k) {
-                    acc_add(D[3 * sym(k, k) + j], t);
+                    put(3 * sym(k, k) + j, t);
                 } else if (j == k) {
-                    acc_add(D[3 * sym(j, l) + j], ff_scale(t, 2.0f));
-                    acc_add(D[3 * sym(j, j) + l], ff_neg(t));
+                    put(3 * sym(j, l) + j, ff_scale(t, 2.0f));
+                    put(3 * sym(j, j) + l, ff_neg(t));
                 } else {
-                    acc_add(D[3 * sym(j, l) + k], t);
-                    acc_add(D[3 * sym(l, k) + j], t);
-                    acc_add(D[3 * sym(j, k) + l], ff_neg(t));
+                    put(3 * sym(j, l) + k, t);
+                    put(3 * sym(l, k) + j, t);
+                    put(3 * sym(j, k) + l, ff_neg(t));
                 }
             }
 #pragma unroll
