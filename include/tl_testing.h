@@ -10,6 +10,13 @@
  *         = a b + c d + e f                           (the contraction kernel's dot product)
  * All pointers are DEVICE arrays of n doubles (b..f may be NULL when the op does not read them); the
  * work is enqueued on `stream`.  Returns a tl_status code (0 = OK).
+ *
+ * tl_testing_f32_staged_stall runs the staged binary32 forward kernel over the full 512-point tiles of
+ * n points with every stage announcing 16 bytes more than its copies deliver, so that no stage
+ * completes: each block's bounded wait runs out (after about 0.5 s), the block counts it in the
+ * counter tl_wait_timeouts reads, waits (bounded again) for the copies it issued, and leaves without
+ * writing outputs.  Tables as for tl_dtg_forward with TL_F32 (inputs 16-byte aligned, else
+ * TL_ERR_ALIGNMENT).  Exercises the failure path of the waits without a device fault.
  */
 #ifndef TL_TESTING_H
 #define TL_TESTING_H
@@ -20,6 +27,8 @@ extern "C" {
 
 TL_API tl_status tl_testing_ff(int op, const double *a, const double *b, const double *c, const double *d,
                                const double *e, const double *f, double *y, int64_t n, tl_stream stream);
+TL_API tl_status tl_testing_f32_staged_stall(const tl_dtg_in *in, const tl_dtg_out *out, int64_t n,
+                                             tl_stream stream);
 
 #ifdef __cplusplus
 }

@@ -33,23 +33,37 @@ __device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32
                  : "memory");
 }
 
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+// One poll; the thread may be suspended for up to about `suspend_ns` while the phase is incomplete.
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity, uint32_t suspend_ns)
 {
     uint32_t done;
-    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n}"
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\tselp.u32 %0, 1, 0, p;\n}"
                  : "=r"(done)
-                 : "r"(smem_addr(bar)), "r"(parity)
+                 : "r"(smem_addr(bar)), "r"(parity), "r"(suspend_ns)
                  : "memory");
     return done != 0;
 }
 
-// Wait for the phase of `bar` with the given parity to complete; false after `polls` unsuccessful
-// polls (each poll may itself block for a short, hardware-defined time), so no wait is unbounded.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32_t polls)
+__device__ __forceinline__ uint64_t global_ns()
 {
-    for (uint32_t i = 0; i < polls; ++i)
-        if (mbar_try_wait(bar, parity))
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for the phase of `bar` with the given parity to complete.  Bounded twice over: at most `polls`
+// polls of at most ~1 us each, and at most `limit_ns` of wall-clock time; false when either runs out.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32_t polls, uint64_t limit_ns)
+{
+    if (mbar_try_wait(bar, parity, 1000))
+        return true;
+    const uint64_t t0 = global_ns();
+    for (uint32_t i = 1; i < polls; ++i) {
+        if (mbar_try_wait(bar, parity, 1000))
             return true;
+        if (global_ns() - t0 > limit_ns)
+            return false;
+    }
     return false;
 }
 

@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(kFwdThreads) dtg_fwd_f32_kernel(const FwdArgs<
 // are brought into shared memory by the bulk-copy engine, STAGES tiles ahead of the threads that
 // compute on them: one thread issues 43 copies of TILE * 4 contiguous bytes per tile, completion is
 // counted in bytes on one mbarrier per stage, and the loads overlap the arithmetic of earlier tiles.
-// 512 points x 2 stages (176 KB: one block, 16 warps per SM) measured best, 0.96 ms at N = 2^24
+// 512 points x 2 stages (176 KB: one block, 16 warps per SM) measured best, 0.94 ms at N = 2^24
 // against 1.00 ms for the plain kernel; 256 x 4 and 384 x 3 (8 and 12 warps) leave the binary64
 // inverse latency-bound, and 640 x 2 or 768 x 2 (K and alpha then read directly) were slower.
 // Each block walks tiles blockIdx.x, + gridDim.x, ...
@@ -147,10 +147,13 @@ __global__ void __launch_bounds__(kFwdThreads) dtg_fwd_f32_kernel(const FwdArgs<
 // points are left to the plain kernel.
 __device__ unsigned int g_wait_timeouts;   // waits that gave up (a bulk copy never completed)
 
-constexpr uint32_t kWaitPolls = 1u << 18;
+constexpr uint32_t kWaitPolls = 1u << 20;
+constexpr uint64_t kWaitNs = 500000000ull;   // 0.5 s: a stage normally lands within microseconds
 
+// extra_tx: bytes announced beyond what is copied; 0 in use.  The test hook passes a nonzero value so
+// that no stage ever completes and the bounded waits run out (the failure path, without any fault).
 template <int TILE, int STAGES>
-__global__ void __launch_bounds__(TILE) dtg_fwd_f32_staged_kernel(const FwdArgs<float> a, int64_t ntiles)
+__global__ void __launch_bounds__(TILE) dtg_fwd_f32_staged_kernel(const FwdArgs<float> a, int64_t ntiles, uint32_t extra_tx)
 {
     extern __shared__ __align__(128) float stage_buf[];   // [STAGES][N_IN][TILE]
     __shared__ __align__(8) uint64_t full[STAGES];
@@ -167,7 +170,7 @@ __global__ void __launch_bounds__(TILE) dtg_fwd_f32_staged_kernel(const FwdArgs<
         const int s = (int)(i % STAGES);
         const int64_t t = (int64_t)blockIdx.x + i * gridDim.x;
         float *dst = stage_buf + (size_t)s * N_IN * TILE;
-        mbar_arrive_expect_tx(&full[s], N_IN * TILE * (uint32_t)sizeof(float));
+        mbar_arrive_expect_tx(&full[s], N_IN * TILE * (uint32_t)sizeof(float) + extra_tx);
 #pragma unroll 1
         for (int k = 0; k < N_IN; ++k)
             bulk_copy_g2s(dst + k * TILE, a.in[k] + t * TILE, TILE * (uint32_t)sizeof(float), &full[s]);
@@ -177,12 +180,12 @@ __global__ void __launch_bounds__(TILE) dtg_fwd_f32_staged_kernel(const FwdArgs<
             issue(i);
     for (int64_t i = 0; i < count; ++i) {
         const int s = (int)(i % STAGES);
-        const bool ok = mbar_wait(&full[s], (uint32_t)((i / STAGES) & 1), kWaitPolls);
+        const bool ok = mbar_wait(&full[s], (uint32_t)((i / STAGES) & 1), kWaitPolls, kWaitNs);
         if (__syncthreads_or(!ok)) {   // block-uniform: record, let issued copies land, leave
             if (tid == 0) {
                 atomicAdd(&g_wait_timeouts, 1u);
                 for (int64_t j = i; j < count && j < i + STAGES - 1; ++j)
-                    mbar_wait(&full[j % STAGES], (uint32_t)((j / STAGES) & 1), kWaitPolls);
+                    mbar_wait(&full[j % STAGES], (uint32_t)((j / STAGES) & 1), kWaitPolls, kWaitNs);
             }
             return;
         }
@@ -200,7 +203,8 @@ __global__ void __launch_bounds__(TILE) dtg_fwd_f32_staged_kernel(const FwdArgs<
 }
 
 template <int TILE, int STAGES>
-static cudaError_t launch_f32_staged(const FwdArgs<float> &a, int64_t ntiles, int sms, cudaStream_t s)
+static cudaError_t launch_f32_staged(const FwdArgs<float> &a, int64_t ntiles, int sms, cudaStream_t s,
+                                     uint32_t extra_tx = 0)
 {
     const size_t smem = (size_t)STAGES * N_IN * TILE * sizeof(float);
     auto kern = dtg_fwd_f32_staged_kernel<TILE, STAGES>;
@@ -211,8 +215,14 @@ static cudaError_t launch_f32_staged(const FwdArgs<float> &a, int64_t ntiles, in
     if (e != cudaSuccess)
         return e;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)sms * std::max(blocks, 1)));
-    kern<<<grid, TILE, smem, s>>>(a, ntiles);
+    kern<<<grid, TILE, smem, s>>>(a, ntiles, extra_tx);
     return cudaGetLastError();
+}
+
+cudaError_t launch_fwd_f32_staged_stalled(const FwdArgs<float> &a, int64_t n, int sms, cudaStream_t s)
+{
+    return n / kF32StagedTile > 0 ? launch_f32_staged<kF32StagedTile, kF32StagedStages>(a, n / kF32StagedTile, sms, s, 16)
+                                  : cudaSuccess;
 }
 
 cudaError_t read_wait_timeouts(unsigned int *count)

@@ -9,6 +9,7 @@
 
 #include "../../include/tl.h"
 #include "tl_host.h"
+#include "../../include/tl_testing.h"
 #include "tl_kernels.h"
 
 namespace tl {
@@ -330,6 +331,21 @@ tl_status tl_dtg_forward(const tl_dtg_in *in, const tl_dtg_out *out, int64_t n, 
     if ((s = device_info(&d)) != TL_OK)
         return s;
     return launch_forward(*d, in, out, n, dtype, (cudaStream_t)stream);
+}
+
+tl_status tl_testing_f32_staged_stall(const tl_dtg_in *in, const tl_dtg_out *out, int64_t n, tl_stream stream)
+{
+    tl_status s = check_forward(in, out, n, TL_F32);
+    if (s != TL_OK || n == 0)
+        return s;
+    for (int k = 0; k < N_IN; ++k)
+        if ((uintptr_t)((const void *const *)in)[k] % 16 != 0)
+            return fail(TL_ERR_ALIGNMENT, "the staged kernel needs 16-byte aligned inputs");
+    const DeviceInfo *d = nullptr;
+    if ((s = device_info(&d)) != TL_OK)
+        return s;
+    const cudaError_t e = launch_fwd_f32_staged_stalled(fwd_args<float>(in, out), n, d->sms, (cudaStream_t)stream);
+    return e == cudaSuccess ? TL_OK : cuda_fail(e, "staged kernel launch");
 }
 
 tl_status tl_dtg_backward(const tl_dtg_in *in, const tl_dtg_gout *gout, const tl_dtg_gin *gin, int64_t n,

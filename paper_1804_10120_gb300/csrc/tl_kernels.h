@@ -18,6 +18,9 @@ cudaError_t launch_fwd_f32(const FwdArgs<float> &a, int64_t n, int grid, cudaStr
 constexpr int kF32StagedTile = 512;
 constexpr int kF32StagedStages = 2;
 cudaError_t launch_fwd_f32_staged(const FwdArgs<float> &a, int64_t n, int sms, int tail_grid, cudaStream_t s);
+// Test hook: the staged kernel over the full tiles of n points with 16 bytes announced per stage that
+// never arrive, so every block's first wait runs out (about 1 s) and the block leaves without output.
+cudaError_t launch_fwd_f32_staged_stalled(const FwdArgs<float> &a, int64_t n, int sms, cudaStream_t s);
 // Number of bounded waits in the staged kernels that gave up since the library was loaded.
 cudaError_t read_wait_timeouts(unsigned int *count);
 cudaError_t launch_fwd_ff(const FwdArgs<double> &a, int64_t n, int grid, cudaStream_t s);
