@@ -285,3 +285,25 @@ def test_f32_staged_equals_plain_kernel_bitwise(n):
     err = component_errors(ya.cpu().numpy()[:, idx].astype(np.float64), oracle.forward(x[:, idx].astype(np.float64)))
     assert err.max() <= TOL_F32_COMPUTE
     assert tl.tl_wait_timeouts() == timeouts
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f64_ff", "f32"])
+def test_single_grid_forward_in_cuda_graph(dtype):
+    """Each forward form captured in a CUDA graph (the staged binary32 kernel included: its launch
+    sets a function attribute, which is not a stream operation) replays to the eager result, bit for
+    bit, with a ragged tail."""
+    import paper_1804_10120_gb300 as tl
+    n = 5 * 512 * 152 + 300
+    td = torch.float32 if dtype == "f32" else torch.float64
+    x = torch.from_numpy(gridgen.random_grid(n, 46)).to(dev(), td)
+    y_eager = tl.tl_dtg_forward(x, dtype=dtype)
+    y = torch.empty_like(y_eager)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        tl.tl_dtg_forward(x, y, dtype=dtype, stream=s)
+    g.replay()
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(y, y_eager)
