@@ -27,6 +27,15 @@ extern "C" {
 
 TL_API tl_status tl_testing_ff(int op, const double *a, const double *b, const double *c, const double *d,
                                const double *e, const double *f, double *y, int64_t n, tl_stream stream);
+/*
+ * tl_testing_f64_int applies one binary64 operation elementwise, as the kernels' integer-pipe form or
+ * the hardware instruction, so the integer forms can be checked bit for bit:
+ *   op 0: y[i] = a[i] * b[i]           (integer-pipe product, mul_int)
+ *   op 3: y[i] = fma(a[i], b[i], c[i]) (hardware fused multiply-add, reference)
+ * (ops 1 and 2 are reserved).  DEVICE arrays of n doubles; c only for op 3.  Enqueued on `stream`.
+ */
+TL_API tl_status tl_testing_f64_int(int op, const double *a, const double *b, const double *c, double *y, int64_t n,
+                                    tl_stream stream);
 TL_API tl_status tl_testing_f32_staged_stall(const tl_dtg_in *in, const tl_dtg_out *out, int64_t n,
                                              tl_stream stream);
 

@@ -25,8 +25,10 @@ template <typename T> __device__ __forceinline__ T ld_opt(const T *p, int64_t x)
     return p ? ld_stream(p + x) : T(0);
 }
 
-// kU: upstream gradient of nabla beta present; kG: upstream gradient of g^ij present.
-template <bool kU, bool kG> __device__ __forceinline__ void bwd_point_f64(const BwdArgs<double> &a, int64_t x)
+// kU: upstream gradient of nabla beta present; kG: upstream gradient of g^ij present.  kIntMul: the 68
+// products not fused into an FMA run on the integer pipes (mul_int, the same bits as the FP64 multiply).
+template <bool kU, bool kG, bool kIntMul = true>
+__device__ __forceinline__ void bwd_point_f64(const BwdArgs<double> &a, int64_t x)
 {
     // ---- recompute: inverse metric, bracket, Christoffel symbols
     const double g00 = ld_stream(a.in[IN_G + 0] + x), g01 = ld_stream(a.in[IN_G + 1] + x),
@@ -39,17 +41,17 @@ template <bool kU, bool kG> __device__ __forceinline__ void bwd_point_f64(const 
     double H[6], h[6];
     {
         double c[6];
-        c[0] = fma(g11, g22, -(g12 * g12));
-        c[1] = fma(g02, g12, -(g01 * g22));
-        c[2] = fma(g01, g12, -(g02 * g11));
-        c[3] = fma(g00, g22, -(g02 * g02));
-        c[4] = fma(g01, g02, -(g00 * g12));
-        c[5] = fma(g00, g11, -(g01 * g01));
-        const double det = fma(g00, c[0], fma(g01, c[1], g02 * c[2]));
+        c[0] = fma(g11, g22, -mul64<kIntMul>(g12, g12));
+        c[1] = fma(g02, g12, -mul64<kIntMul>(g01, g22));
+        c[2] = fma(g01, g12, -mul64<kIntMul>(g02, g11));
+        c[3] = fma(g00, g22, -mul64<kIntMul>(g02, g02));
+        c[4] = fma(g01, g02, -mul64<kIntMul>(g00, g12));
+        c[5] = fma(g00, g11, -mul64<kIntMul>(g01, g01));
+        const double det = fma(g00, c[0], fma(g01, c[1], mul64<kIntMul>(g02, c[2])));
         const double rdet = rcp_f64(det);
 #pragma unroll
         for (int p = 0; p < 6; ++p) {
-            H[p] = c[p] * rdet;
+            H[p] = mul64<kIntMul>(c[p], rdet);
             h[p] = half_exact(H[p]);
         }
     }
@@ -65,8 +67,8 @@ template <bool kU, bool kG> __device__ __forceinline__ void bwd_point_f64(const 
     for (int p = 0; p < 6; ++p) {
         W[p] = ld_opt(a.gout[OUT_DTG + p], x);
         const double K = ld_stream(a.in[IN_K + p] + x);
-        st_stream(a.gin[IN_K + p] + x, m2a * W[p]);
-        asum = (p == 0) ? K * W[p] : fma(K, W[p], asum);
+        st_stream(a.gin[IN_K + p] + x, mul64<kIntMul>(m2a, W[p]));
+        asum = (p == 0) ? mul64<kIntMul>(K, W[p]) : fma(K, W[p], asum);
     }
     st_stream(a.gin[IN_ALPHA] + x, -twice_exact(asum));
 
@@ -100,7 +102,7 @@ template <bool kU, bool kG> __device__ __forceinline__ void bwd_point_f64(const 
     double u[3], beta[3];
 #pragma unroll
     for (int l = 0; l < 3; ++l) {
-        double s = S[0] * T[l][0];
+        double s = mul64<kIntMul>(S[0], T[l][0]);
 #pragma unroll
         for (int p = 1; p < 6; ++p)
             s = fma(S[p], T[l][p], s);
@@ -109,7 +111,8 @@ template <bool kU, bool kG> __device__ __forceinline__ void bwd_point_f64(const 
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         beta[k] = ld_stream(a.in[IN_BETA + k] + x);
-        st_stream(a.gin[IN_BETA + k] + x, -fma(h[sym(k, 2)], u[2], fma(h[sym(k, 1)], u[1], h[sym(k, 0)] * u[0])));
+        st_stream(a.gin[IN_BETA + k] + x,
+                  -fma(h[sym(k, 2)], u[2], fma(h[sym(k, 1)], u[1], mul64<kIntMul>(h[sym(k, 0)], u[0]))));
     }
 
     // ---- Gamma: Gammabar = V - beta_k S_p
@@ -126,7 +129,7 @@ template <bool kU, bool kG> __device__ __forceinline__ void bwd_point_f64(const 
     for (int i = 0; i < 3; ++i)
 #pragma unroll
         for (int l = 0; l < 3; ++l) {
-            double s = gbar[i][0] * T[l][0];
+            double s = mul64<kIntMul>(gbar[i][0], T[l][0]);
 #pragma unroll
             for (int p = 1; p < 6; ++p)
                 s = fma(gbar[i][p], T[l][p], s);
@@ -137,7 +140,8 @@ template <bool kU, bool kG> __device__ __forceinline__ void bwd_point_f64(const 
     for (int l = 0; l < 3; ++l)
 #pragma unroll
         for (int p = 0; p < 6; ++p)
-            Tb[l][p] = fma(h[sym(2, l)], gbar[2][p], fma(h[sym(1, l)], gbar[1][p], h[sym(0, l)] * gbar[0][p]));
+            Tb[l][p] = fma(h[sym(2, l)], gbar[2][p],
+                           fma(h[sym(1, l)], gbar[1][p], mul64<kIntMul>(h[sym(0, l)], gbar[0][p])));
 
     // ---- bracket -> d_k g_ij: every T_lp term of Eq. 6 scattered onto the stored derivative it reads.
     // The first contribution to an entry is assigned rather than added to zero (an FP64 add saved per
@@ -190,12 +194,13 @@ template <bool kU, bool kG> __device__ __forceinline__ void bwd_point_f64(const 
     for (int i = 0; i < 3; ++i)
 #pragma unroll
         for (int j = 0; j < 3; ++j)
-            M[i][j] = fma(H[sym(i, 2)], A[sym(2, j)], fma(H[sym(i, 1)], A[sym(1, j)], H[sym(i, 0)] * A[sym(0, j)]));
+            M[i][j] = fma(H[sym(i, 2)], A[sym(2, j)],
+                          fma(H[sym(i, 1)], A[sym(1, j)], mul64<kIntMul>(H[sym(i, 0)], A[sym(0, j)])));
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
         for (int j = i; j < 3; ++j) {
-            const double v = fma(M[i][2], H[sym(2, j)], fma(M[i][1], H[sym(1, j)], M[i][0] * H[sym(0, j)]));
+            const double v = fma(M[i][2], H[sym(2, j)], fma(M[i][1], H[sym(1, j)], mul64<kIntMul>(M[i][0], H[sym(0, j)])));
             st_stream(a.gin[IN_G + sym(i, j)] + x, (i == j) ? -half_exact(v) : -v);
         }
 }
@@ -209,7 +214,7 @@ template <bool kU, bool kG> __device__ __forceinline__ void bwd_point_f64(const 
 template <bool kU, bool kG>
 __device__ __noinline__ void bwd_point_f64_general(const BwdArgs<double> &a, int64_t x)
 {
-    bwd_point_f64<kU, kG>(a, x);
+    bwd_point_f64<kU, kG, false>(a, x);
 }
 
 template <bool kU, bool kG> __device__ __forceinline__ void bwd_point_ff(const BwdArgs<double> &a, int64_t x)

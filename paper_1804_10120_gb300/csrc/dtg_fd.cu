@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(256, 2) dtg_fd_kernel(const FdArgs a, int64_t 
             double v[N_IN];
             fd_inputs<ORDER, UNIFORM>(a, x, xo, rn, v);
             if (!FF || !chain_ff<FdArgs, UNIFORM>(v, a, x, a.c1[0]))
-                chain_f64<FdArgs, UNIFORM>(v, a, x, a.c1[0]);
+                chain_f64<FdArgs, UNIFORM, !FF>(v, a, x, a.c1[0]);
         }
     }
 }

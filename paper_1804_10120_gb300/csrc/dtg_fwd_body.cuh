@@ -39,12 +39,21 @@ __device__ __forceinline__ void christoffel_bracket(const R (&dg)[18], R (&T)[3]
 }
 
 // ------------------------------------------------------------------------------------ binary64 forward
+// Product for the binary64 chain: on the integer pipes (mul_int, bit-identical to the FP64 multiply)
+// where the FP64 pipe is the binding unit; the FP64 multiply in rarely taken fallback paths, whose
+// register needs would otherwise raise those of the kernels that call them.
+template <bool kIntMul> __device__ __forceinline__ double mul64(double a, double b)
+{
+    return kIntMul ? mul_int(a, b) : a * b;
+}
+
 // The chain on one point's 43 input values (already in registers, in the input-table order); the 39
 // outputs go to o.out[s][x] (o: any argument block with an `out` table).  kScaled: the d_k g_ij and
 // d_j beta_i entries of v are differences that still need one common factor sd (a finite-difference
 // stencil on a grid with equal spacings); sd is then applied once to 1/2 g^il and fused into
-// nabla_j beta_i instead of to each of the 27 derivatives.
-template <class OutTable, bool kScaled = false>
+// nabla_j beta_i instead of to each of the 27 derivatives.  kIntMul: the 31 products that are not
+// fused into an FMA go to the integer pipes (mul_int); the results are the same bits either way.
+template <class OutTable, bool kScaled = false, bool kIntMul = true>
 __device__ __forceinline__ void chain_f64(const double (&v)[N_IN], const OutTable &o, int64_t x, double sd = 1.0)
 {
     // step 1: inverse metric by cofactors; det by first-row expansion
@@ -57,18 +66,18 @@ __device__ __forceinline__ void chain_f64(const double (&v)[N_IN], const OutTabl
         dg[s] = v[IN_DG + s];
 
     double c[6];
-    c[0] = fma(g11, g22, -(g12 * g12));
-    c[1] = fma(g02, g12, -(g01 * g22));
-    c[2] = fma(g01, g12, -(g02 * g11));
-    c[3] = fma(g00, g22, -(g02 * g02));
-    c[4] = fma(g01, g02, -(g00 * g12));
-    c[5] = fma(g00, g11, -(g01 * g01));
-    const double det = fma(g00, c[0], fma(g01, c[1], g02 * c[2]));
+    c[0] = fma(g11, g22, -mul64<kIntMul>(g12, g12));
+    c[1] = fma(g02, g12, -mul64<kIntMul>(g01, g22));
+    c[2] = fma(g01, g12, -mul64<kIntMul>(g02, g11));
+    c[3] = fma(g00, g22, -mul64<kIntMul>(g02, g02));
+    c[4] = fma(g01, g02, -mul64<kIntMul>(g00, g12));
+    c[5] = fma(g00, g11, -mul64<kIntMul>(g01, g01));
+    const double det = fma(g00, c[0], fma(g01, c[1], mul64<kIntMul>(g02, c[2])));
     const double rdet = rcp_f64(det);
     double ginv[6], h[6];
 #pragma unroll
     for (int p = 0; p < 6; ++p) {
-        ginv[p] = c[p] * rdet;
+        ginv[p] = mul64<kIntMul>(c[p], rdet);
         if constexpr (kScaled)
             h[p] = ginv[p] * half_exact(sd);
         else
@@ -84,7 +93,7 @@ __device__ __forceinline__ void chain_f64(const double (&v)[N_IN], const OutTabl
     for (int i = 0; i < 3; ++i)
 #pragma unroll
         for (int p = 0; p < 6; ++p) {
-            gam[i][p] = fma(h[sym(i, 2)], T[2][p], fma(h[sym(i, 1)], T[1][p], h[sym(i, 0)] * T[0][p]));
+            gam[i][p] = fma(h[sym(i, 2)], T[2][p], fma(h[sym(i, 1)], T[1][p], mul64<kIntMul>(h[sym(i, 0)], T[0][p])));
             st_stream(o.out[OUT_GAMMA + 6 * i + p] + x, gam[i][p]);
         }
 
@@ -123,14 +132,14 @@ __device__ __forceinline__ void chain_f64(const double (&v)[N_IN], const OutTabl
         }
 }
 
-__device__ __forceinline__ void fwd_point_f64(const FwdArgs<double> &a, int64_t x)
+template <bool kIntMul = true> __device__ __forceinline__ void fwd_point_f64(const FwdArgs<double> &a, int64_t x)
 {
     double v[N_IN];
 #pragma unroll
     for (int s = 0; s < N_IN; ++s)
         v[s] = ld_stream(a.in[s] + x);
     asm volatile("" ::: "memory");   // every load is issued before any arithmetic
-    chain_f64(v, a, x);
+    chain_f64<FwdArgs<double>, false, kIntMul>(v, a, x);
 }
 
 }  // namespace tl

@@ -21,7 +21,7 @@
 namespace tl {
 
 // The all-binary64 evaluation, out of line (only points outside the pair format's range take it).
-__device__ __noinline__ void fwd_point_f64_general(const FwdArgs<double> &a, int64_t x) { fwd_point_f64(a, x); }
+__device__ __noinline__ void fwd_point_f64_general(const FwdArgs<double> &a, int64_t x) { fwd_point_f64<false>(a, x); }
 
 __device__ __forceinline__ void fwd_point_ff(const FwdArgs<double> &a, int64_t x)
 {
@@ -116,5 +116,34 @@ extern "C" TL_API tl_status tl_testing_ff(int op, const double *a, const double 
         return TL_OK;
     const int grid = (int)std::min<int64_t>((n + 255) / 256, 4096);
     tl::ff_testing_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(op, a, b, c, d, e, f, y, n);
+    return cudaGetLastError() == cudaSuccess ? TL_OK : TL_ERR_CUDA;
+}
+
+// The integer-pipe binary64 operations against the hardware ones (tl_testing.h).
+namespace tl {
+
+__global__ void f64_int_testing_kernel(int op, const double *a, const double *b, const double *c, double *y,
+                                       int64_t n)
+{
+    const GridStride gs;
+    for (int64_t i = gs.first; i < n; i += gs.step) {
+        if (op == 0)
+            y[i] = mul_int(a[i], b[i]);
+        else
+            y[i] = fma(a[i], b[i], c[i]);
+    }
+}
+
+}  // namespace tl
+
+extern "C" TL_API tl_status tl_testing_f64_int(int op, const double *a, const double *b, const double *c, double *y,
+                                               int64_t n, tl_stream stream)
+{
+    if (op < 0 || op > 3 || op == 1 || op == 2 || n < 0 || !a || !b || !y || (op == 3 && !c))
+        return TL_ERR_INVALID_ARG;
+    if (n == 0)
+        return TL_OK;
+    const int grid = (int)std::min<int64_t>((n + 255) / 256, 4096);
+    tl::f64_int_testing_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(op, a, b, c, y, n);
     return cudaGetLastError() == cudaSuccess ? TL_OK : TL_ERR_CUDA;
 }

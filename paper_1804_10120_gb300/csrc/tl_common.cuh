@@ -110,6 +110,39 @@ __device__ __forceinline__ double neg_exact(double x)
     return __hiloint2double(__double2hiint(x) ^ (int)0x80000000, __double2loint(x));
 }
 
+// ---- IEEE binary64 multiplication on the integer pipes --------------------------------------------------
+// The FP64 pipe is the binding unit of the binary64 kernels while the integer pipes are nearly idle, so
+// some products are formed from the operands' bits: the 106-bit product of the two 53-bit significands
+// (two 64-bit integer multiplies), normalised by at most one bit and rounded to nearest-even from the
+// bits below the 53 kept -- the definition of the IEEE 754 product, so the result equals a * b bit for
+// bit.  Normal operands with a normal result take this path; a zero operand times a finite one gives
+// the signed zero; every other case (subnormal, inf, nan, a result near overflow or underflow) calls
+// a * b out of line, so no predicated FP64 multiply is left in the common path.
+static __device__ __noinline__ double mul_slow(double a, double b) { return a * b; }
+
+__device__ __forceinline__ double mul_int(double a, double b)
+{
+    const uint64_t ua = (uint64_t)__double_as_longlong(a), ub = (uint64_t)__double_as_longlong(b);
+    const uint32_t ea = (uint32_t)(ua >> 52) & 0x7ffu, eb = (uint32_t)(ub >> 52) & 0x7ffu;
+    const int e = (int)(ea + eb) - 1023;   // biased exponent of the product, before the normalising shift
+    const uint64_t sign = (ua ^ ub) & 0x8000000000000000ull;
+    if (ea - 1u < 2046u && eb - 1u < 2046u && e >= 1 && e <= 2044) {
+        const uint64_t ma = (ua & 0x000fffffffffffffull) | 0x0010000000000000ull;
+        const uint64_t mb = (ub & 0x000fffffffffffffull) | 0x0010000000000000ull;
+        const uint64_t lo = ma * mb, hi = __umul64hi(ma, mb);    // product in [2^104, 2^106)
+        const uint32_t t = (uint32_t)(hi >> 41);                  // 1 when the product is >= 2^105
+        const uint32_t sh = 52u + t;
+        uint64_t m = (hi << (12u - t)) | (lo >> sh);              // the 53 kept bits
+        const uint64_t rem = lo & ((1ull << sh) - 1ull), half = 1ull << (sh - 1u);
+        m += (rem > half || (rem == half && (m & 1ull))) ? 1ull : 0ull;
+        // m in [2^52, 2^53]: its leading bit adds one to the exponent field, a rounding carry one more
+        return __longlong_as_double((long long)(sign | (((uint64_t)(e + (int)t - 1) << 52) + m)));
+    }
+    if (((ua << 1) == 0ull && eb != 0x7ffu) || ((ub << 1) == 0ull && ea != 0x7ffu))
+        return __longlong_as_double((long long)sign);
+    return mul_slow(a, b);
+}
+
 // ---- binary64 reciprocal ------------------------------------------------------------------------------
 // Seed: binary32 reciprocal (MUFU) of the binary32 truncation of d, both conversions done on integer
 // bits; relative seed error e0 < 2^-21.  One third-order Newton-Raphson step in binary64,
