@@ -79,7 +79,7 @@ __device__ __forceinline__ void chain_f64(const double (&v)[N_IN], const OutTabl
     for (int p = 0; p < 6; ++p) {
         ginv[p] = mul64<kIntMul>(c[p], rdet);
         if constexpr (kScaled)
-            h[p] = ginv[p] * half_exact(sd);
+            h[p] = mul64<kIntMul>(ginv[p], half_exact(sd));
         else
             h[p] = half_exact(ginv[p]);      // 1/2 g^il of Eq. 6
         st_stream(o.out[OUT_GINV + p] + x, ginv[p]);
@@ -104,7 +104,7 @@ __device__ __forceinline__ void chain_f64(const double (&v)[N_IN], const OutTabl
     if constexpr (kScaled) {
 #pragma unroll
         for (int p = 0; p < 6; ++p)           // Gamma^k_ij beta_k is symmetric in ij: 6 sums
-            S6[p] = fma(gam[2][p], b2, fma(gam[1][p], b1, gam[0][p] * b0));
+            S6[p] = fma(gam[2][p], b2, fma(gam[1][p], b1, mul64<kIntMul>(gam[0][p], b0)));
     }
 #pragma unroll
     for (int i = 0; i < 3; ++i)
