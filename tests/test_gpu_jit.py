@@ -111,16 +111,18 @@ def test_generated_product_is_the_ieee_product():
     k.close()
 
 
-def test_generated_chain_equals_hand_kernel_gamma_bitwise():
-    """The generator emits the chain's contractions as the hand kernel does (one stand-alone product,
-    then FMAs in the same order), so the Christoffel symbols agree bit for bit."""
+def test_generated_chain_emits_fused_contractions():
+    """The generated chain uses one integer-pipe product per contraction and FMAs for the rest (31
+    stand-alone products, like the hand kernel), a Newton reciprocal for 1/det, and agrees with the
+    hand kernel within the binary64 gate."""
     import paper_1804_10120_gb300 as tl
     from paper_1804_10120_gb300.programs import CHAIN
     k = tl.JitKernel(CHAIN)
+    body = k.source[k.source.index("tl_jit_kernel"):]
+    assert body.count("tl_mul(") == 31 and body.count("tl_rcp(") == 1 and " / " not in body
     xd = torch.from_numpy(gridgen.random_grid(100003, 5)).to(dev())
     y_gen = k.launch(xd)
     y_hand = tl.tl_dtg_forward(xd)
     torch.cuda.synchronize()
-    assert torch.equal(y_gen[6:24], y_hand[6:24]) or component_errors(y_gen.cpu().numpy(), y_hand.cpu().numpy()).max() <= TOL_F64
     assert component_errors(y_gen.cpu().numpy(), y_hand.cpu().numpy()).max() <= TOL_F64
     k.close()
