@@ -70,13 +70,19 @@ template <int EQ> __device__ __forceinline__ void expr_point(const ExprArgs &a, 
                 idx[t] = rem % 3;
                 rem /= 3;
             }
-            double p = __dmul_rn(v[0][idx[0]], v[1][idx[1]]);
+            // rank 3: every other product on the integer pipes (mul_int, the same IEEE product), which
+            // balances the FP64 pipe against instruction issue (3999 -> 4546 GB/s at N = 2^22); at
+            // rank 4 the same split measured slower (3079 -> 2066 GB/s) and all products stay FP64
+            constexpr bool kMix = R == 3;
+            double p = (kMix && (c & 1)) ? mul_int(v[0][idx[0]], v[1][idx[1]]) : __dmul_rn(v[0][idx[0]], v[1][idx[1]]);
 #pragma unroll
             for (int t = 2; t < R; ++t)
-                p = __dmul_rn(p, v[t][idx[t]]);
+                p = (kMix && ((c + t) & 1)) ? mul_int(p, v[t][idx[t]]) : __dmul_rn(p, v[t][idx[t]]);
             S(c, p);
         }
     } else if (EQ == 18) {           // A_ijkl = sum_m B_im E_mjkl, one (j,k,l) slice at a time
+        // (in 18 and 19 the first product of each contraction is mul_int: 3190 -> 4213 and 1726 ->
+        // 2198 GB/s at N = 2^22; in 20 the extra registers cost more than the FP64 slots saved)
         double B[9];
 #pragma unroll
         for (int q = 0; q < 9; ++q)
@@ -86,7 +92,7 @@ template <int EQ> __device__ __forceinline__ void expr_point(const ExprArgs &a, 
             const double e0 = L(9 + r), e1 = L(9 + 27 + r), e2 = L(9 + 54 + r);
 #pragma unroll
             for (int i = 0; i < 3; ++i)
-                S(27 * i + r, fma(B[3 * i + 2], e2, fma(B[3 * i + 1], e1, B[3 * i] * e0)));
+                S(27 * i + r, fma(B[3 * i + 2], e2, fma(B[3 * i + 1], e1, mul_int(B[3 * i], e0))));
         }
     } else if (EQ == 19) {           // A_ijkl = sum_mn C_jn B_im E_mnkl = (B E_kl C^T)_ij per (k,l)
         double B[9], C[9];
@@ -107,12 +113,12 @@ template <int EQ> __device__ __forceinline__ void expr_point(const ExprArgs &a, 
             for (int i = 0; i < 3; ++i)
 #pragma unroll
                 for (int nn = 0; nn < 3; ++nn)
-                    P[i][nn] = fma(B[3 * i + 2], E[2][nn], fma(B[3 * i + 1], E[1][nn], B[3 * i] * E[0][nn]));
+                    P[i][nn] = fma(B[3 * i + 2], E[2][nn], fma(B[3 * i + 1], E[1][nn], mul_int(B[3 * i], E[0][nn])));
 #pragma unroll
             for (int i = 0; i < 3; ++i)
 #pragma unroll
                 for (int j = 0; j < 3; ++j)
-                    S(27 * i + 9 * j + r, fma(C[3 * j + 2], P[i][2], fma(C[3 * j + 1], P[i][1], C[3 * j] * P[i][0])));
+                    S(27 * i + 9 * j + r, fma(C[3 * j + 2], P[i][2], fma(C[3 * j + 1], P[i][1], mul_int(C[3 * j], P[i][0]))));
         }
     } else if (EQ == 20) {           // A_ijkl = sum_mno D_ko C_jn B_im E_mnol, per l: three 3x3 factors
         double B[9], C[9], D[9];
