@@ -744,14 +744,15 @@ const char *const kMulSource =
     "  const unsigned ea = (unsigned)(ua >> 52) & 0x7ffu, eb = (unsigned)(ub >> 52) & 0x7ffu;\n"
     "  const int e = (int)(ea + eb) - 1023;\n"
     "  const unsigned long long sign = (ua ^ ub) & 0x8000000000000000ull;\n"
-    "  if (ea - 1u < 2046u && eb - 1u < 2046u && e >= 1 && e <= 2044) {\n"
+    "  if (ea - 1u < 2046u && eb - 1u < 2046u && (unsigned)(e - 1) < 2044u) {\n"
     "    const unsigned long long ma = (ua & 0x000fffffffffffffull) | 0x0010000000000000ull;\n"
     "    const unsigned long long mb = (ub & 0x000fffffffffffffull) | 0x0010000000000000ull;\n"
     "    const unsigned long long lo = ma * mb, hi = __umul64hi(ma, mb);\n"
-    "    const unsigned t = (unsigned)(hi >> 41), sh = 52u + t;\n"
-    "    unsigned long long m = (hi << (12u - t)) | (lo >> sh);\n"
-    "    const unsigned long long rem = lo & ((1ull << sh) - 1ull), half = 1ull << (sh - 1u);\n"
-    "    m += (rem > half || (rem == half && (m & 1ull))) ? 1ull : 0ull;\n"
+    "    const unsigned t = (unsigned)(hi >> 41);\n"
+    "    const unsigned long long h = t ? hi : (hi << 1) | (lo >> 63), l = t ? lo : lo << 1;\n"
+    "    unsigned long long m = (h << 11) | (l >> 53);\n"
+    "    const unsigned long long rem = l & 0x001fffffffffffffull;\n"
+    "    m += (rem + (m & 1ull) > 0x0010000000000000ull) ? 1ull : 0ull;\n"
     "    return __longlong_as_double((long long)(sign | (((unsigned long long)(e + (int)t - 1) << 52) + m)));\n"
     "  }\n"
     "  if (((ua << 1) == 0ull && eb != 0x7ffu) || ((ub << 1) == 0ull && ea != 0x7ffu))\n"

@@ -126,15 +126,16 @@ __device__ __forceinline__ double mul_int(double a, double b)
     const uint32_t ea = (uint32_t)(ua >> 52) & 0x7ffu, eb = (uint32_t)(ub >> 52) & 0x7ffu;
     const int e = (int)(ea + eb) - 1023;   // biased exponent of the product, before the normalising shift
     const uint64_t sign = (ua ^ ub) & 0x8000000000000000ull;
-    if (ea - 1u < 2046u && eb - 1u < 2046u && e >= 1 && e <= 2044) {
+    if (ea - 1u < 2046u && eb - 1u < 2046u && (uint32_t)(e - 1) < 2044u) {
         const uint64_t ma = (ua & 0x000fffffffffffffull) | 0x0010000000000000ull;
         const uint64_t mb = (ub & 0x000fffffffffffffull) | 0x0010000000000000ull;
         const uint64_t lo = ma * mb, hi = __umul64hi(ma, mb);    // product in [2^104, 2^106)
         const uint32_t t = (uint32_t)(hi >> 41);                  // 1 when the product is >= 2^105
-        const uint32_t sh = 52u + t;
-        uint64_t m = (hi << (12u - t)) | (lo >> sh);              // the 53 kept bits
-        const uint64_t rem = lo & ((1ull << sh) - 1ull), half = 1ull << (sh - 1u);
-        m += (rem > half || (rem == half && (m & 1ull))) ? 1ull : 0ull;
+        // normalise to [2^105, 2^106): one bit left unless it is there already
+        const uint64_t h = t ? hi : (hi << 1) | (lo >> 63), l = t ? lo : lo << 1;
+        uint64_t m = (h << 11) | (l >> 53);                       // the 53 kept bits
+        const uint64_t rem = l & 0x001fffffffffffffull;           // the 53 discarded bits
+        m += (rem + (m & 1ull) > 0x0010000000000000ull) ? 1ull : 0ull;   // nearest, ties to even
         // m in [2^52, 2^53]: its leading bit adds one to the exponent field, a rounding carry one more
         return __longlong_as_double((long long)(sign | (((uint64_t)(e + (int)t - 1) << 52) + m)));
     }
