@@ -649,6 +649,8 @@ def main():
                        "parallelism": "replicas (independent grids per GPU)" if world > 1 else "single GPU",
                        "l2": "inputs+outputs %.1f GB > 129 MB L2; no flush" % (82 * n * esz / 1e9)},
             "roofline": roofline,
+            # per-step spread, as the paper reports its runs (median of the timed steps, with min and max)
+            "step_ms": {"median": statistics.median(per), "min": min(per), "max": max(per)},
             "gpu_launches": args.steps,
             "clocks": clk.summary(),
             "e2e": e2e,
