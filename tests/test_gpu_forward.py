@@ -307,3 +307,27 @@ def test_single_grid_forward_in_cuda_graph(dtype):
     g.replay()
     torch.cuda.synchronize()
     assert torch.equal(y, y_eager)
+
+
+def test_integer_pipe_products_equal_fp64_products_on_extreme_values():
+    """The binary64 kernel forms its stand-alone products on the integer pipes; the float-float
+    kernel's fallback path evaluates the same chain with FP64 multiplies.  With beta_0 = 1e30 every
+    point takes that fallback, so on inputs full of zeros, subnormals, huge values, infinities and
+    NaNs (products overflowing, underflowing, special) the two must agree bit for bit."""
+    import paper_1804_10120_gb300 as tl
+    n = 1 << 16
+    rng = np.random.default_rng(11)
+    x = gridgen.random_grid(n, 47)
+    specials = np.array([0.0, -0.0, 5e-324, -2.5e-310, 1e-160, 3e-155, 1e155, -7e160, 1e300, np.inf,
+                         -np.inf, np.nan, 2.0 ** 1023, 2.0 ** -1022])
+    pts = rng.integers(0, n, n // 2)
+    comps = rng.integers(0, 43, n // 2)
+    x[comps, pts] = specials[rng.integers(0, len(specials), n // 2)]
+    scale = 2.0 ** rng.integers(-500, 500, n)      # whole points scaled towards both thresholds
+    x[:, : n // 4] *= scale[: n // 4]
+    x[31] = 1e30                                   # beta_0 outside the pair range: every point falls back
+    y64 = run_f64(x, "f64")
+    yff = run_f64(x, "f64_ff")
+    assert np.array_equal(np.isnan(y64), np.isnan(yff))
+    ok = np.isnan(y64) | (y64.view(np.uint64) == yff.view(np.uint64))
+    assert ok.all(), np.argwhere(~ok)[:5]
