@@ -332,3 +332,26 @@ def test_integer_pipe_products_equal_fp64_products_on_extreme_values():
     assert np.array_equal(np.isnan(y64), np.isnan(yff))
     ok = np.isnan(y64) | (y64.view(np.uint64) == yff.view(np.uint64))
     assert ok.all(), np.argwhere(~ok)[:5]
+
+
+def test_f32_full_size_sampled_and_conformal_256():
+    """The binary32 workloads at full size in the benchmark's launch configuration (the staged kernel:
+    16-byte aligned rows of a [43, 2^24] buffer): N = 2^24 random grid (seed 4) and the conformal 256^3
+    grid, each checked on 65536 sampled points against the oracle on the binary32-rounded inputs;
+    every output written; the conformal grid's exact zeros stay exact everywhere."""
+    import paper_1804_10120_gb300 as tl
+    n = 1 << 24
+    rng = np.random.default_rng(4)
+    idx = np.unique(np.concatenate([np.arange(1024), np.arange(n - 1024, n), rng.integers(0, n, 63488)]))
+    for x in (gridgen.random_grid(n, 4).astype(np.float32), gridgen.conformal_grid(256).astype(np.float32)):
+        xd = torch.from_numpy(x).to(dev())
+        assert xd[1].data_ptr() % 16 == 0
+        y = tl.tl_dtg_forward(xd, dtype="f32")
+        torch.cuda.synchronize()
+        ys = y[:, torch.from_numpy(idx).to(dev())].cpu().numpy().astype(np.float64)
+        err = component_errors(ys, oracle.forward(np.ascontiguousarray(x[:, idx]).astype(np.float64)))
+        assert err.max() <= TOL_F32_COMPUTE, dict(zip(OUT_NAMES, err))
+        assert bool(torch.isfinite(y).all())
+        del xd, y
+    y = tl.tl_dtg_forward(torch.from_numpy(x).to(dev()), dtype="f32")
+    assert bool((y[24:39] == 0).all())              # conformal: dbcov and dtg vanish exactly
