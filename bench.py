@@ -349,7 +349,8 @@ def extras(dev, stream, steps, x64, hbm):
             tl.tl_dtg_forward(xd, yd, stream=side_stream)
     ms_sepg = cuda_time(g2.replay, max(2, steps // 2), torch.cuda.current_stream(dev))
     out["batched"] = {"workload": "600 subgrids, N_d = n^3, n ~ U{8..48} (seed 2), %d points" % tot,
-                      "config": {"threads": cfg[0], "blocks_per_sm": cfg[1]},
+                      "config": {"threads": cfg[0], "blocks_per_sm": cfg[1],
+                                 "points_per_thread": plan.points_per_thread},
                       "ms": ms_b, "points_per_s": tot / ms_b * 1e3, "GB_s": 656 * tot / ms_b / 1e6,
                       "hbm_frac": 656 * tot / ms_b / 1e6 / hbm,
                       "ms_in_graph": ms_bg,

@@ -130,9 +130,12 @@ TL_API tl_status tl_dtg_forward_host(const tl_dtg_in *in, const tl_dtg_out *out,
  * must stay alive.  Calling it with another device current returns TL_ERR_PLAN_MISMATCH.
  *
  * tl_dtg_batched_tune times the candidate configurations (threads per block 128/256/512 x resident blocks
- * per SM) by launching the plan on `stream` (so it writes the outputs), keeps the fastest in the plan and
- * records it in the tuning cache: the file named by TL_TUNE_CACHE, else $HOME/.cache/tl_dtg_tune.txt
- * (TL_TUNE_CACHE=off disables the cache).  It synchronises `stream`.
+ * per SM x points per thread 1/2/4; a tile of a grid is threads x points-per-thread points) by launching
+ * the plan on `stream` (so it writes the outputs), keeps the fastest in the plan and records it in the
+ * tuning cache: the file named by TL_TUNE_CACHE, else $HOME/.cache/tl_dtg_tune.txt (TL_TUNE_CACHE=off
+ * disables the cache).  It synchronises `stream`.  tl_batch_plan_config / tl_batch_plan_set_config read
+ * and set threads and blocks per SM (TL_ERR_INVALID_ARG beyond the kernel's occupancy);
+ * tl_batch_plan_points_per_thread / tl_batch_plan_set_points_per_thread the points per thread (1, 2 or 4).
  *
  * tl_batch_plan_check synchronises the plan's device and returns the status word recorded by its
  * launches (TL_OK, or TL_ERR_PLAN_MISMATCH if a launch found the plan inconsistent), then clears it.
@@ -144,6 +147,8 @@ TL_API tl_status tl_dtg_batched(const tl_batch_plan *plan, tl_stream stream);
 TL_API tl_status tl_dtg_batched_tune(tl_batch_plan *plan, tl_stream stream);
 TL_API tl_status tl_batch_plan_config(const tl_batch_plan *plan, int32_t *threads, int32_t *blocks_per_sm);
 TL_API tl_status tl_batch_plan_set_config(tl_batch_plan *plan, int32_t threads, int32_t blocks_per_sm);
+TL_API tl_status tl_batch_plan_points_per_thread(const tl_batch_plan *plan, int32_t *points_per_thread);
+TL_API tl_status tl_batch_plan_set_points_per_thread(tl_batch_plan *plan, int32_t points_per_thread);
 TL_API tl_status tl_batch_plan_check(const tl_batch_plan *plan);
 TL_API void tl_batch_plan_destroy(tl_batch_plan *plan);
 

@@ -285,11 +285,14 @@ def _batch_lib():
         L.tl_dtg_batched_tune.argtypes = [vp, vp]
         L.tl_batch_plan_config.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]
         L.tl_batch_plan_set_config.argtypes = [vp, i32, i32]
+        L.tl_batch_plan_points_per_thread.argtypes = [vp, ctypes.POINTER(i32)]
+        L.tl_batch_plan_set_points_per_thread.argtypes = [vp, i32]
         L.tl_batch_plan_check.argtypes = [vp]
         L.tl_batch_plan_destroy.argtypes = [vp]
         L.tl_batch_plan_destroy.restype = None
         for f in (L.tl_dtg_batched_prepare, L.tl_dtg_batched, L.tl_dtg_batched_tune, L.tl_batch_plan_config,
-                  L.tl_batch_plan_set_config, L.tl_batch_plan_check):
+                  L.tl_batch_plan_set_config, L.tl_batch_plan_points_per_thread,
+                  L.tl_batch_plan_set_points_per_thread, L.tl_batch_plan_check):
             f.restype = ctypes.c_int
         L._batch_ready = True
     return L
@@ -353,8 +356,16 @@ class BatchPlan:
         _check(_batch_lib().tl_batch_plan_config(self._h, ctypes.byref(t), ctypes.byref(b)))
         return t.value, b.value
 
-    def set_config(self, threads, blocks_per_sm):
+    def set_config(self, threads, blocks_per_sm, points_per_thread=None):
         _check(_batch_lib().tl_batch_plan_set_config(self._h, threads, blocks_per_sm))
+        if points_per_thread is not None:
+            _check(_batch_lib().tl_batch_plan_set_points_per_thread(self._h, points_per_thread))
+
+    @property
+    def points_per_thread(self):
+        q = ctypes.c_int32()
+        _check(_batch_lib().tl_batch_plan_points_per_thread(self._h, ctypes.byref(q)))
+        return q.value
 
     def check(self):
         import torch

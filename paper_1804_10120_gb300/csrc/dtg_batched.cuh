@@ -1,8 +1,9 @@
 // dtg_batched.cuh -- persistent multi-grid loop shared by the batched forward kernels.
 //
 // Many subgrids of uneven size (the paper's multi-domain grids, Sec. 1) run in ONE launch.  The plan
-// cuts every grid into tiles of blockDim.x points and lays the tiles of all grids end to end; CTA c
-// takes a contiguous run of about total_tiles / gridDim.x tiles, so it crosses few grid boundaries.
+// cuts every grid into tiles of blockDim.x x ppt points (ppt points per thread, strided by blockDim.x)
+// and lays the tiles of all grids end to end; CTA c takes a contiguous run of about
+// total_tiles / gridDim.x tiles, so it crosses few grid boundaries.
 // The component pointer tables of all grids live in device memory (uploaded once by the plan, like the
 // paper's cached GPUPointers, Sec. 4); a CTA copies the table of its current grid into shared memory
 // only when it crosses into a new grid, and the per-point bodies read their pointers from there.
@@ -18,6 +19,7 @@ struct BatchView {
     const int64_t *tile_prefix;    // G + 1 running tile counts for this block size
     int64_t total_tiles;
     int32_t G;
+    int32_t ppt;                   // points per thread in a tile (the tile holds blockDim.x x ppt points)
     uint32_t *status;              // 0 = fine; a TL_ERR_* code if the plan looked inconsistent
 };
 
@@ -54,9 +56,13 @@ __device__ __forceinline__ void batched_loop(const BatchView &v, FwdArgs<T> &s_a
             __syncthreads();
             loaded = d;
         }
-        const int64_t x = (t - v.tile_prefix[d]) * blockDim.x + threadIdx.x;
-        if (x < v.n[d])
-            body(s_args, x);
+        const int64_t x0 = (t - v.tile_prefix[d]) * ((int64_t)blockDim.x * v.ppt) + threadIdx.x;
+#pragma unroll 1
+        for (int k = 0; k < v.ppt; ++k) {
+            const int64_t x = x0 + (int64_t)k * blockDim.x;
+            if (x < v.n[d])
+                body(s_args, x);
+        }
     }
 }
 

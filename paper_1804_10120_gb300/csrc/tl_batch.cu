@@ -20,6 +20,7 @@ namespace {
 
 constexpr uint64_t kPlanMagic = 0x746c5f706c616e31ull;   // "tl_plan1"
 constexpr int kThreadOptions[3] = {128, 256, 512};
+constexpr int kPptOptions[3] = {1, 2, 4};   // points per thread in a tile
 
 int thread_slot(int threads)
 {
@@ -29,7 +30,15 @@ int thread_slot(int threads)
     return -1;
 }
 
-// ---- tuning cache: one line per key, "key threads blocks_per_sm ms" -----------------------------------
+int ppt_slot(int ppt)
+{
+    for (int i = 0; i < 3; ++i)
+        if (kPptOptions[i] == ppt)
+            return i;
+    return -1;
+}
+
+// ---- tuning cache: one line per key, "key threads blocks_per_sm points_per_thread ms" ------------------
 std::mutex g_cache_mu;
 
 std::string cache_path()
@@ -43,7 +52,7 @@ std::string cache_path()
     return std::string(home) + "/.cache/tl_dtg_tune.txt";
 }
 
-bool cache_lookup(const std::string &key, int *threads, int *bps)
+bool cache_lookup(const std::string &key, int *threads, int *bps, int *ppt)
 {
     std::lock_guard<std::mutex> lk(g_cache_mu);
     const std::string path = cache_path();
@@ -52,21 +61,23 @@ bool cache_lookup(const std::string &key, int *threads, int *bps)
     FILE *f = fopen(path.c_str(), "r");
     if (!f)
         return false;
-    char k[512];
-    int t = 0, b = 0;
+    char line[768], k[512];
+    int t = 0, b = 0, q = 0;
     double ms = 0;
     bool found = false;
-    while (fscanf(f, "%511s %d %d %lf", k, &t, &b, &ms) == 4)
-        if (key == k && thread_slot(t) >= 0 && b >= 1) {
+    while (fgets(line, sizeof line, f))
+        if (sscanf(line, "%511s %d %d %d %lf", k, &t, &b, &q, &ms) == 5 && key == k && thread_slot(t) >= 0 &&
+            b >= 1 && ppt_slot(q) >= 0) {
             *threads = t;
             *bps = b;
+            *ppt = q;
             found = true;          // the last entry for a key wins
         }
     fclose(f);
     return found;
 }
 
-void cache_store(const std::string &key, int threads, int bps, double ms)
+void cache_store(const std::string &key, int threads, int bps, int ppt, double ms)
 {
     std::lock_guard<std::mutex> lk(g_cache_mu);
     const std::string path = cache_path();
@@ -76,7 +87,7 @@ void cache_store(const std::string &key, int threads, int bps, double ms)
     if (slash != std::string::npos && slash > 0)
         mkdir(path.substr(0, slash).c_str(), 0755);   // one level; EEXIST is fine
     if (FILE *f = fopen(path.c_str(), "a")) {
-        fprintf(f, "%s %d %d %.6f\n", key.c_str(), threads, bps, ms);
+        fprintf(f, "%s %d %d %d %.6f\n", key.c_str(), threads, bps, ppt, ms);
         fclose(f);
     }
 }
@@ -93,13 +104,14 @@ struct tl_batch_plan {
     int sms = 0;
     int max_blocks[3] = {0, 0, 0};          // occupancy per thread option
     int threads = 256, blocks_per_sm = 0;   // launch configuration
+    int ppt = 1;                            // points per thread in a tile
     std::string key;                        // tuning-cache key
     // device data
     void **d_tables = nullptr;              // G x 82
     int64_t *d_n = nullptr;                 // G
-    int64_t *d_prefix = nullptr;            // 3 x (G + 1)
+    int64_t *d_prefix = nullptr;            // 9 x (G + 1): thread option x points-per-thread option
     uint32_t *d_status = nullptr;
-    int64_t total_tiles[3] = {0, 0, 0};
+    int64_t total_tiles[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
 };
 
 using namespace tl;
@@ -124,6 +136,7 @@ static BatchView view_of(const tl_batch_plan *p, int slot)
     v.n = p->d_n;
     v.tile_prefix = p->d_prefix + (size_t)slot * (p->G + 1);
     v.total_tiles = p->total_tiles[slot];
+    v.ppt = kPptOptions[slot % 3];
     v.G = p->G;
     v.status = p->d_status;
     return v;
@@ -193,12 +206,13 @@ tl_status tl_dtg_batched_prepare(const tl_dtg_in *in, const tl_dtg_out *out, con
         memcpy(&tables[(size_t)d * (N_IN + N_OUT)], &in[d], N_IN * sizeof(void *));
         memcpy(&tables[(size_t)d * (N_IN + N_OUT) + N_IN], &out[d], N_OUT * sizeof(void *));
     }
-    std::vector<int64_t> prefix((size_t)3 * (G + 1));
-    for (int i = 0; i < 3; ++i) {
+    std::vector<int64_t> prefix((size_t)9 * (G + 1));
+    for (int i = 0; i < 9; ++i) {
+        const int64_t tile = (int64_t)kThreadOptions[i / 3] * kPptOptions[i % 3];
         int64_t acc = 0;
         for (int32_t d = 0; d < G; ++d) {
             prefix[(size_t)i * (G + 1) + d] = acc;
-            acc += (n[d] + kThreadOptions[i] - 1) / kThreadOptions[i];
+            acc += (n[d] + tile - 1) / tile;
         }
         prefix[(size_t)i * (G + 1) + G] = acc;
         p->total_tiles[i] = acc;
@@ -225,15 +239,17 @@ tl_status tl_dtg_batched_prepare(const tl_dtg_in *in, const tl_dtg_out *out, con
     }
     // tuning-cache key: GPU, SMs, dtype, batch shape (G and the size of the batch in powers of two)
     char key[512];
-    snprintf(key, sizeof key, "%s|sm%d|dtype%d|batched|G%d|log2pts%d", di->name, di->sms, (int)dtype, (int)G,
+    snprintf(key, sizeof key, "%s|sm%d|dtype%d|batched2|G%d|log2pts%d", di->name, di->sms, (int)dtype, (int)G,
              total > 0 ? (int)std::floor(std::log2((double)total)) : 0);
     p->key = key;
     p->threads = 256;
     p->blocks_per_sm = p->max_blocks[1];
-    int t = 0, b = 0;
-    if (cache_lookup(p->key, &t, &b) && b <= p->max_blocks[thread_slot(t)]) {
+    p->ppt = 1;
+    int t = 0, b = 0, q = 0;
+    if (cache_lookup(p->key, &t, &b, &q) && b <= p->max_blocks[thread_slot(t)]) {
         p->threads = t;
         p->blocks_per_sm = b;
+        p->ppt = q;
     }
     p->magic = kPlanMagic;
     *plan = p;
@@ -245,7 +261,7 @@ tl_status tl_dtg_batched(const tl_batch_plan *p, tl_stream stream)
     tl_status s = plan_ok(p);
     if (s != TL_OK)
         return s;
-    const int slot = thread_slot(p->threads);
+    const int slot = thread_slot(p->threads) * 3 + ppt_slot(p->ppt);
     if (p->total_tiles[slot] == 0)
         return TL_OK;
     const int64_t want = (int64_t)p->sms * p->blocks_per_sm;
@@ -282,6 +298,25 @@ tl_status tl_batch_plan_set_config(tl_batch_plan *p, int32_t threads, int32_t bl
     return TL_OK;
 }
 
+tl_status tl_batch_plan_points_per_thread(const tl_batch_plan *p, int32_t *ppt)
+{
+    if (!p || p->magic != kPlanMagic)
+        return fail(TL_ERR_PLAN_MISMATCH, "not a live batch plan");
+    if (ppt)
+        *ppt = p->ppt;
+    return TL_OK;
+}
+
+tl_status tl_batch_plan_set_points_per_thread(tl_batch_plan *p, int32_t ppt)
+{
+    if (!p || p->magic != kPlanMagic)
+        return fail(TL_ERR_PLAN_MISMATCH, "not a live batch plan");
+    if (ppt_slot(ppt) < 0)
+        return fail(TL_ERR_INVALID_ARG, "points per thread must be 1, 2 or 4 (got %d)", (int)ppt);
+    p->ppt = ppt;
+    return TL_OK;
+}
+
 tl_status tl_dtg_batched_tune(tl_batch_plan *p, tl_stream stream)
 {
     tl_status s = plan_ok(p);
@@ -292,11 +327,11 @@ tl_status tl_dtg_batched_tune(tl_batch_plan *p, tl_stream stream)
     cudaError_t e;
     if ((e = cudaEventCreate(&e0)) != cudaSuccess || (e = cudaEventCreate(&e1)) != cudaSuccess)
         return cuda_fail(e, "cudaEventCreate");
-    const int keep_t = p->threads, keep_b = p->blocks_per_sm;
-    int best_t = keep_t, best_b = keep_b;
+    const int keep_t = p->threads, keep_b = p->blocks_per_sm, keep_q = p->ppt;
+    int best_t = keep_t, best_b = keep_b, best_q = keep_q;
     float best = 1e30f;
-    for (int i = 0; i < 3 && s == TL_OK; ++i) {
-        const int T = kThreadOptions[i];
+    for (int j = 0; j < 9 && s == TL_OK; ++j) {
+        const int i = j / 3, T = kThreadOptions[i], Q = kPptOptions[j % 3];
         int cands[4] = {1, 2, 4, p->max_blocks[i]};
         for (int c = 0; c < 4 && s == TL_OK; ++c) {
             const int B = cands[c];
@@ -304,6 +339,7 @@ tl_status tl_dtg_batched_tune(tl_batch_plan *p, tl_stream stream)
                 continue;
             p->threads = T;
             p->blocks_per_sm = B;
+            p->ppt = Q;
             if ((s = tl_dtg_batched(p, stream)) != TL_OK)   // warm-up
                 break;
             cudaEventRecord(e0, st);
@@ -320,6 +356,7 @@ tl_status tl_dtg_batched_tune(tl_batch_plan *p, tl_stream stream)
                 best = ms;
                 best_t = T;
                 best_b = B;
+                best_q = Q;
             }
         }
     }
@@ -327,8 +364,9 @@ tl_status tl_dtg_batched_tune(tl_batch_plan *p, tl_stream stream)
     cudaEventDestroy(e1);
     p->threads = best_t;
     p->blocks_per_sm = best_b;
+    p->ppt = best_q;
     if (s == TL_OK && best < 1e30f)
-        cache_store(p->key, best_t, best_b, best / 3.0);
+        cache_store(p->key, best_t, best_b, best_q, best / 3.0);
     return s;
 }
 

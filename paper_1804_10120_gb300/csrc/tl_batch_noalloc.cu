@@ -143,6 +143,7 @@ extern "C" TL_API tl_status tl_dtg_batched_noalloc(const tl_dtg_in *in, const tl
     v.n = (const int64_t *)(dsc + kTablesBytes);
     v.tile_prefix = (const int64_t *)(dsc + kTablesBytes + kNBytes);
     v.total_tiles = tiles;
+    v.ppt = 1;
     v.G = G;
     v.status = (uint32_t *)(dsc + kStatusOffset);
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)D.sms * D.blocks[dtype], tiles));

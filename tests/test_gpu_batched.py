@@ -53,17 +53,21 @@ def test_every_config_and_graph_capture():
     torch.cuda.synchronize()
     for threads in (128, 256, 512):
         for bps in (1, 2):
-            for y in ys:
-                y.fill_(float("nan"))
-            try:
-                plan.set_config(threads, bps)
-            except tl.TLError as e:              # beyond this kernel's occupancy
-                assert e.status == 1
-                continue
-            plan.launch()
-            torch.cuda.synchronize()
-            for y, r in zip(ys, refs):
-                assert torch.equal(y, r), (threads, bps)
+            for ppt in (1, 2, 4):
+                for y in ys:
+                    y.fill_(float("nan"))
+                try:
+                    plan.set_config(threads, bps, ppt)
+                except tl.TLError as e:          # beyond this kernel's occupancy
+                    assert e.status == 1
+                    continue
+                assert plan.points_per_thread == ppt
+                plan.launch()
+                torch.cuda.synchronize()
+                for y, r in zip(ys, refs):
+                    assert torch.equal(y, r), (threads, bps, ppt)
+    with pytest.raises(tl.TLError):
+        plan.set_config(256, 1, 3)
     # CUDA graph: capture one launch, replay twice
     for y in ys:
         y.fill_(float("nan"))
@@ -87,11 +91,12 @@ def test_tuner_picks_a_valid_config(tmp_path, monkeypatch):
     hosts, xs, ys = make_batch(sides, 23)
     plan = tl.BatchPlan(xs, ys)
     t, b = plan.tune()
-    assert t in (128, 256, 512) and b >= 1
+    q = plan.points_per_thread
+    assert t in (128, 256, 512) and b >= 1 and q in (1, 2, 4)
     text = (tmp_path / "tune.txt").read_text()
-    assert "batched" in text and ("%d %d" % (t, b)) in text
+    assert "batched" in text and ("%d %d %d" % (t, b, q)) in text
     plan2 = tl.BatchPlan(xs, ys)             # same shape: configuration from the cache
-    assert plan2.config == (t, b)
+    assert plan2.config == (t, b) and plan2.points_per_thread == q
     plan2.launch()
     torch.cuda.synchronize()
     for x, y in zip(hosts, ys):
