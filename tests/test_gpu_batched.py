@@ -140,3 +140,43 @@ def test_f32_batch():
     plan.launch()
     for x, y in zip(xs, ys):
         assert torch.equal(tl.tl_dtg_forward(x, dtype="f32"), y)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f64_ff", "f32"])
+def test_array_and_scattered_row_tables(dtype):
+    """Grids given as [43, n] / [39, n] arrays, as rows of a buffer at irregular offsets, and a batch
+    mixing both all give the single-grid result bit for bit (the plan keeps one pointer per table
+    entry whatever the layout)."""
+    import paper_1804_10120_gb300 as tl
+    td = torch.float32 if dtype == "f32" else torch.float64
+    sides = [int(s) for s in np.random.default_rng(6).integers(3, 24, 30)]
+    hosts, xs, ys = make_batch(sides, 24, td)
+    refs = [tl.tl_dtg_forward(x, dtype=dtype) for x in xs]
+    def scattered(count, n):
+        # rows of one buffer at offsets that are not equally spaced
+        offs = [k * (n + 64) + (k % 3) * 8 for k in range(count)]
+        buf = torch.full((offs[-1] + n + 8,), float("nan"), dtype=td, device=dev())
+        return [buf[o:o + n] for o in offs]
+    rows_x = []
+    for x in xs:
+        r = scattered(43, x.shape[1])
+        for k in range(43):
+            r[k].copy_(x[k])
+        rows_x.append(r)
+    rows_y = [scattered(39, y.shape[1]) for y in ys]
+    mixed_x = [rows_x[d] if d % 2 else xs[d] for d in range(len(xs))]
+    mixed_y = [rows_y[d] if d % 2 else ys[d] for d in range(len(ys))]
+    for bx, by in ((xs, ys), (rows_x, rows_y), (mixed_x, mixed_y)):
+        for y in by:
+            for r in (y if isinstance(y, list) else [y]):
+                r.fill_(float("nan"))
+        plan = tl.BatchPlan(bx, by, dtype=dtype)
+        for ppt in (1, 4):
+            plan.set_config(*plan.config, ppt)
+            plan.launch()
+            torch.cuda.synchronize()
+            for y, r in zip(by, refs):
+                got = torch.stack(y) if isinstance(y, list) else y
+                assert torch.equal(got, r), (dtype, ppt)
+        plan.check()
+        plan.close()
