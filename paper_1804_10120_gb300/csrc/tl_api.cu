@@ -378,7 +378,7 @@ tl_status tl_dtg_backward(const tl_dtg_in *in, const tl_dtg_gout *gout, const tl
         a.gout[q] = (const double *)((const void *const *)gout)[q];
     cudaError_t e = (dtype == TL_F64)
                         ? launch_bwd_f64(a, n, grid_for(n, kBwdThreads, d->sms, d->bwd_f64_blocks), (cudaStream_t)stream)
-                        : launch_bwd_ff(a, n, grid_for(n, kBwdThreads, d->sms, d->bwd_ff_blocks), (cudaStream_t)stream);
+                        : launch_bwd_ff(a, n, grid_for(n, kBwdFfThreads, d->sms, d->bwd_ff_blocks), (cudaStream_t)stream);
     if (e == cudaErrorNotSupported)
         return fail(TL_ERR_UNSUPPORTED, "dtype %d has no adjoint kernel in this build", (int)dtype);
     if (e != cudaSuccess)

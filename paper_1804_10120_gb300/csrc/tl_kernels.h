@@ -9,6 +9,7 @@ namespace tl {
 constexpr int kFwdThreads = 256;
 
 constexpr int kBwdThreads = 128;
+constexpr int kBwdFfThreads = 256;   // the float-float adjoint (one block per SM, see dtg_bwd.cu)
 
 cudaError_t launch_fwd_f64(const FwdArgs<double> &a, int64_t n, int grid, cudaStream_t s);
 cudaError_t launch_fwd_f32(const FwdArgs<float> &a, int64_t n, int grid, cudaStream_t s);
