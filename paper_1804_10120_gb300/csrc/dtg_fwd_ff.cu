@@ -34,11 +34,16 @@ __device__ __forceinline__ void fwd_point_ff(const FwdArgs<double> &a, int64_t x
         fwd_point_f64_general(a, x);
 }
 
-__global__ void __launch_bounds__(kFwdThreads) dtg_fwd_ff_kernel(const FwdArgs<double> a, int64_t n)
+// Blocks walk block-sized strides with a barrier per point, which keeps a block's warps on the same
+// stretch of the ~3000-instruction body (2.47 -> 2.43 ms at N = 2^24; the same walk lifted the
+// float-float adjoint, whose body is twice as long, by 11 %).  The trip count depends only on the block.
+__global__ void __launch_bounds__(kFwdThreads, 2) dtg_fwd_ff_kernel(const FwdArgs<double> a, int64_t n)
 {
-    const GridStride gs;
-    for (int64_t x = gs.first; x < n; x += gs.step)
-        fwd_point_ff(a, x);
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
+        if (base + threadIdx.x < n)
+            fwd_point_ff(a, base + threadIdx.x);
+        __syncthreads();
+    }
 }
 
 cudaError_t launch_fwd_ff(const FwdArgs<double> &a, int64_t n, int grid, cudaStream_t s)
