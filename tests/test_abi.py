@@ -113,3 +113,20 @@ def test_batched_prepare_argument_checks(L):
     assert L.tl_dtg_batched_prepare(ctypes.byref(ins), ctypes.byref(outs), ctypes.byref(neg), G, 0, ctypes.byref(h)) == 1
     assert L.tl_dtg_batched_prepare(ctypes.byref(ins), ctypes.byref(outs), ctypes.byref(ns), -1, 0, ctypes.byref(h)) == 1
     assert L.tl_dtg_batched_prepare(ctypes.byref(ins), ctypes.byref(outs), ctypes.byref(ns), G, 9, ctypes.byref(h)) == 1
+
+
+def test_bench_traffic_is_tied_to_kernel_sources(monkeypatch, tmp_path):
+    """bench.py reports an ncu DRAM figure only for the kernel sources it was captured on: scaled to
+    the benchmark's point count when the recorded source digest matches, None otherwise."""
+    import json
+    import bench
+    kernel = "dtg_fwd_f64_kernel"
+    entry = {"dram_bytes": 4.0e9, "n": 1 << 22, "src_digest": bench.src_digest(kernel), "ncu_duration_s": 1e-3}
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "profiles" / "traffic.json").write_text(json.dumps({kernel: entry}))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "src_digest", lambda k=None: entry["src_digest"])
+    assert bench.traffic_per_launch(kernel, 1 << 24) == 4 * 4.0e9
+    monkeypatch.setattr(bench, "src_digest", lambda k=None: "changed")
+    assert bench.traffic_per_launch(kernel, 1 << 24) is None
+    assert bench.traffic_per_launch("no_such_kernel", 1 << 24) is None
