@@ -355,3 +355,23 @@ def test_f32_full_size_sampled_and_conformal_256():
         del xd, y
     y = tl.tl_dtg_forward(torch.from_numpy(x).to(dev()), dtype="f32")
     assert bool((y[24:39] == 0).all())              # conformal: dbcov and dtg vanish exactly
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f64_ff"])
+def test_singular_metric_matches_oracle_special_values(dtype):
+    """The degenerate case of the method: a singular metric (det g = 0; rank 2 and rank 1, and the same
+    metrics negated).  g^ij = cofactor / det becomes +-inf or NaN and propagates through every output;
+    the kernel's reciprocal-times-cofactor form must give the oracle's pattern of NaN and signed
+    infinities."""
+    n = 64
+    x = gridgen.random_grid(n, 51)
+    rank2 = np.array([1.0, 1.0, 0.0, 1.0, 0.0, 2.0])      # rows 0 and 1 equal
+    rank1 = np.array([1.0, 2.0, 3.0, 4.0, 6.0, 9.0])      # outer product of (1, 2, 3)
+    x[0:6, 0:32] = rank2[:, None]
+    x[0:6, 32:64] = rank1[:, None]
+    x[0:6, 16:32] *= -1.0                                 # the rank-2 metric negated
+    with np.errstate(all="ignore"):
+        y_ref = oracle.forward(x)
+    y = run_f64(x, dtype=dtype)
+    assert np.array_equal(np.isnan(y), np.isnan(y_ref))
+    assert np.array_equal(np.isposinf(y), np.isposinf(y_ref)) and np.array_equal(np.isneginf(y), np.isneginf(y_ref))
