@@ -227,7 +227,7 @@ def reference_arm(args):
     print(json.dumps(line), flush=True)
 
 
-# Algorithmic work per grid point (the design doc derives both):
+# Algorithmic work per grid point:
 #   bytes: 8 x (43 + 39) for binary64, 4 x 82 for binary32 (each component array crosses HBM once);
 #   binary64 flops of the fused chain as this library formulates it (FMA = 2): inverse 35, Eq. 6 bracket
 #   18, Eq. 6 contraction 90, covariant shift derivative 54, Eq. 5 15.
