@@ -230,14 +230,16 @@ def reference_arm(args):
 # Algorithmic work per grid point:
 #   bytes: 8 x (43 + 39) for binary64, 4 x 82 for binary32 (each component array crosses HBM once);
 #   binary64 flops of the fused chain as this library formulates it (FMA = 2): inverse 35, Eq. 6 bracket
-#   18, Eq. 6 contraction 90, covariant shift derivative 54, Eq. 5 15.
-FLOPS_F64_PER_POINT = 212
-FP64_TFLOPS_PEAK = 2 * 2 * 152 * 2.07e9 / 1e12   # 2 DFMA / clk / SM x 2 flop x 152 SMs x 2070 MHz
-# Of the 212 flops, the 31 products that are not fused into an FMA run on the integer pipes (mul_int,
-# bit-identical to the FP64 multiply); the FP64 pipe executes 86 DFMA + 9 DADD = 181 flops per point.
-# The arithmetic roof of this instruction mix is reached when the FP64 pipe is saturated:
-FLOPS_F64_ON_FP64_PIPE = 181
-ALU_TFLOPS_PEAK = FP64_TFLOPS_PEAK * FLOPS_F64_PER_POINT / FLOPS_F64_ON_FP64_PIPE
+#   18, Eq. 6 contraction 90, covariant shift derivative 39 (the 6 distinct sums Gamma^k_ij beta_k and 9
+#   subtractions), Eq. 5 15.
+FLOPS_F64_PER_POINT = 197
+# The FP64 pipe issues 2 operations (DFMA, DADD or DMUL alike) per clock per SM:
+FP64_OPS_PER_S = 2 * 152 * 2.07e9                # x 152 SMs x 2070 MHz
+# Of the 197 flops, the 37 products that are not fused into an FMA run on the integer pipes (mul_int,
+# bit-identical to the FP64 multiply), and the FP64 pipe executes 71 DFMA + 18 DADD = 89 operations per
+# point.  The arithmetic roof of this instruction mix is reached when those 89 operations fill the pipe:
+FP64_OPS_PER_POINT = 89
+ALU_TFLOPS_PEAK = FP64_OPS_PER_S * FLOPS_F64_PER_POINT / FP64_OPS_PER_POINT / 1e12
 
 
 def _max_over_ranks(v, dev):
@@ -588,11 +590,13 @@ def main():
         tf = FLOPS_F64_PER_POINT * n / avg_launch_s / 1e12
         roofline = {"bound": "alu", "achieved": tf, "peak": ALU_TFLOPS_PEAK, "unit": "TFLOP/s",
                     "frac": tf / ALU_TFLOPS_PEAK, "traffic": traffic,
-                    "peak_source": "derived: FP64 pipe 2 DFMA/clk/SM x 2 flop x 152 SMs x 2070 MHz = 1.259 TFLOP/s "
-                                   "carries 181 of the 212 flops per point, the integer pipes the other 31 "
-                                   "(products): roof = 1.259 x 212 / 181",
-                    "fp64_pipe_tflops": FLOPS_F64_ON_FP64_PIPE * n / avg_launch_s / 1e12,
-                    "fp64_pipe_peak": FP64_TFLOPS_PEAK,
+                    "peak_source": "derived: the FP64 pipe issues 2 operations/clk/SM x 152 SMs x 2070 MHz = "
+                                   "629 G operations/s; the chain puts 89 of them per point on it (71 DFMA + "
+                                   "18 DADD; its 37 stand-alone products run on the integer pipes), so its 197 "
+                                   "flops per point cost 89 FP64 issue slots: roof = 629e9 x 197 / 89",
+                    "fp64_pipe": {"ops_per_point": FP64_OPS_PER_POINT,
+                                  "achieved_gops": FP64_OPS_PER_POINT * n / avg_launch_s / 1e9,
+                                  "peak_gops": FP64_OPS_PER_S / 1e9},
                     "kernel": KERNEL_NAME[variant], "flops_per_point": FLOPS_F64_PER_POINT,
                     "avg_launch_ms": avg_launch_s * 1e3,
                     "hbm": {"achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,

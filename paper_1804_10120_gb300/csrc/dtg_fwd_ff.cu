@@ -1,8 +1,8 @@
 // dtg_fwd_ff.cu -- forward chain with float-float contractions (TL_F64_FF).
 //
 // GB300 issues FP64 arithmetic at 1/64 of its FP32 rate (two FP64 operations per clock per SM), and
-// the all-binary64 chain needs 126 binary64 operations per point (95 on the FP64 pipe when its
-// stand-alone products run on the integer pipes): that alone caps it near 45-57 % of the HBM
+// the all-binary64 chain needs 126 binary64 operations per point (89 on the FP64 pipe when its
+// stand-alone products run on the integer pipes): that alone caps it near 48-68 % of the HBM
 // roofline.  This kernel keeps binary64 hardware for the cancellation-prone parts -- the cofactors,
 // determinant and inverse of g_ij, the bracket of Eq. 6 and Eq. 5 itself -- and evaluates the two
 // contractions, Gamma^i_jk = sum_l (g^il / 2) T_ljk (Eq. 6) and sum_k Gamma^k_ij beta_k (footnote to
