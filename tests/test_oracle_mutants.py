@@ -21,6 +21,7 @@ FORWARD_PINS = [
     "test_spherical_coordinates_textbook",
     "test_curvilinear_flat_space_closed_forms",
     "test_killing_field_rotation",
+    "test_shift_derivative_and_eq5_from_the_lie_derivative",
     "test_metric_compatibility",
     "test_packing_convention",
 ]

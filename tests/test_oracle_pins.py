@@ -271,6 +271,28 @@ def test_killing_field_rotation():
     assert np.abs(dtg - (-2 * alpha * K)).max() <= 1e-13
 
 
+def test_shift_derivative_and_eq5_from_the_lie_derivative():
+    """Christoffel-free closed forms on a generic curved grid.  With the vector beta^k = g^kl beta_l,
+    the symmetric part of nabla_j beta_i is half the Lie derivative of the metric along beta^k,
+        L_beta g_ij = beta^k d_k g_ij + g_kj d_i beta^k + g_ik d_j beta^k,
+    with d_i beta^k = -g^ka (d_i g_ab) g^bl beta_l + g^kl d_i beta_l, and its antisymmetric part is that
+    of d_j beta_i (Gamma^k_ij is symmetric in ij).  So nabla_j beta_i = L_ij / 2 + (d_j beta_i -
+    d_i beta_j) / 2 and Eq. 5 gives d_t g_ij = -2 alpha K_ij + L_ij.  The inverse here is numpy's."""
+    x = gridgen.random_grid(4096, 17)
+    G, D, K, alpha, beta, B = unpack_inputs(x)
+    H = np.linalg.inv(G.transpose(2, 0, 1)).transpose(1, 2, 0)
+    bu = np.einsum("kln,ln->kn", H, beta)
+    dbu = -np.einsum("kan,abin,bln,ln->kin", H, D, H, beta) + np.einsum("kln,lin->kin", H, B)
+    L = np.einsum("kn,ijkn->ijn", bu, D) + np.einsum("kjn,kin->ijn", G, dbu) + np.einsum("ikn,kjn->ijn", G, dbu)
+    _, _, Nb, dtg = unpack_outputs(oracle.forward(x))
+    Nb_ref = 0.5 * L + 0.5 * (B - B.transpose(1, 0, 2))
+    dtg_ref = -2.0 * alpha * K + L
+    for i in range(3):
+        for j in range(3):
+            assert normwise(Nb[i, j], Nb_ref[i, j]) <= 1e-14, (i, j)
+            assert normwise(dtg[i, j], dtg_ref[i, j]) <= 1e-14, (i, j)
+
+
 def test_metric_compatibility():
     """nabla_k g_ij = 0:  g_lj Gamma^l_ki + g_il Gamma^l_kj = d_k g_ij for any metric."""
     x = gridgen.random_grid(4096, 0)
