@@ -4,13 +4,13 @@
  * At every point of an N-point grid the library evaluates, in one fused kernel, the chain of
  * Lewis & Pfeiffer, "Automatic generation of CUDA code performing tensor manipulations using C++
  * expression templates" (arXiv:1804.10120):
- *   1. g^ij, the inverse of the symmetric spatial metric g_ij (Sec. 1, after Eq. 6: "the inverse");
+ *   1. g^ij, the inverse of the symmetric spatial metric g_ij (Sec. 1, after Eq. 6);
  *   2. the Christoffel symbols Gamma^i_jk = 1/2 g^il (d_k g_jl + d_j g_lk - d_l g_jk)   (Eq. 6);
  *   3. the covariant derivative of the shift nabla_j beta_i = d_j beta_i - Gamma^k_ij beta_k
  *      (footnote to Listing 1);
  *   4. d_t g_ij = -2 alpha K_ij + nabla_i beta_j + nabla_j beta_i   (Eq. 5);
  * its adjoint (reverse-mode derivative; the paper has none), and a batched form that runs many
- * multi-domain subgrids (Sec. 1: "for multi-domain methods, on multiple spatial grids") in one launch.
+ * multi-domain subgrids (Sec. 1: multi-domain methods evolve several spatial grids) in one launch.
  *
  * Data layout.  Structure of arrays: every tensor component is its own array of n elements (the
  * paper's Tensor<DataMesh>, Sec. 2.2), and a symmetric index pair is stored once (Sec. 2.2, lookup table).

@@ -7,8 +7,8 @@
  *
  * What it computes (Lewis & Pfeiffer, arXiv:1804.10120), one grid point at a time, in IEEE binary64,
  * compiled with floating-point contraction disabled:
- *   1. g^ij, the inverse of the symmetric 3x3 spatial metric g_ij (the paper only says "the inverse",
- *      Sec. 1 after Eq. 6).  Written out as adjugate / determinant, the determinant by first-row
+ *   1. g^ij, the inverse of the symmetric 3x3 spatial metric g_ij (the paper names it and gives no
+ *      method, Sec. 1 after Eq. 6).  Written out as adjugate / determinant, the determinant by first-row
  *      expansion.
  *   2. The Christoffel symbols of the second kind, Eq. 6:
  *          Gamma^i_jk = 1/2 sum_l g^il (d_k g_jl + d_j g_lk - d_l g_jk),
