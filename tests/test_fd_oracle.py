@@ -19,12 +19,15 @@ def _mode_fields(shape, kvec, phase, which):
 
 
 @pytest.mark.parametrize("order", [2, 4])
-def test_discrete_derivative_of_a_mode_is_exact(order):
+@pytest.mark.parametrize("field,first", [(13, 34), (4, 6 + 3 * 4)], ids=["beta_0", "g_12"])
+def test_discrete_derivative_of_a_mode_is_exact(order, field, first):
     """For sin(k x + phi) the centred differences are exactly cos(k x + phi) times
-    sin(kh)/h (order 2) or (8 sin(kh) - sin(2kh)) / (6h) (order 4)."""
+    sin(kh)/h (order 2) or (8 sin(kh) - sin(2kh)) / (6h) (order 4), along each axis with its own
+    spacing; checked for a shift component (d_j beta_0 at 34 + j) and a metric component
+    (d_k g_12 at 6 + 3 p(1,2) + k)."""
     shape = (20, 12, 10)
     kv = (3, -2, 1)
-    f, c = _mode_fields(shape, kv, 0.7, 13)       # beta_0
+    f, c = _mode_fields(shape, kv, 0.7, field)
     h = (1 / 20, 1 / 12, 1 / 10)
     x = oracle.fd_inputs(f, shape, h, order)
     for axis in range(3):
@@ -33,8 +36,9 @@ def test_discrete_derivative_of_a_mode_is_exact(order):
             factor = np.sin(k * h[axis]) / h[axis]
         else:
             factor = (8 * np.sin(k * h[axis]) - np.sin(2 * k * h[axis])) / (6 * h[axis])
-        assert np.abs(x[34 + axis] - factor * c).max() <= 1e-12 * abs(factor)
-    assert np.all(x[37:43] == 0.0)               # beta_1, beta_2 are zero
+        assert np.abs(x[first + axis] - factor * c).max() <= 1e-12 * abs(factor)
+    others = [r for r in list(range(6, 24)) + list(range(34, 43)) if not first <= r < first + 3]
+    assert np.all(x[others] == 0.0)              # every other derivative entry is zero
 
 
 @pytest.mark.parametrize("order", [2, 4])

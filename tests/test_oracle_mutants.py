@@ -1,8 +1,9 @@
-"""The oracle's pins catch plausible mistakes: each case below plants one mistake (a dropped term, a
-wrong sign, a transposed index or operand, a wrong factor, a storage-order slip) in a copy of the
-oracle's C source, builds the copy, points the oracle module at it and runs the pins of
-test_oracle_pins.py against it.  Every planted mistake must fail at least one pin, and the unchanged
-copy must pass them all.  The committed oracle is never modified (no GPU).
+"""The oracles' pins catch plausible mistakes: each case below plants one mistake (a dropped term, a
+wrong sign, a transposed index or operand, a wrong factor, a storage-order slip) in a copy of one of the
+oracle's C sources, builds the copy, points the oracle module at it and runs the pins of
+test_oracle_pins.py (the chain and its adjoint), test_fd_oracle.py (on-grid derivatives) or
+test_expr_oracle.py (the benchmark expressions) against it.  Every planted mistake must fail at least
+one pin, and the unchanged copy must pass them all.  The committed oracle is never modified (no GPU).
 """
 import os
 import subprocess
@@ -10,9 +11,11 @@ import subprocess
 import pytest
 
 import oracle
+from tests import test_expr_oracle as expr_pins
+from tests import test_fd_oracle as fd_pins
 from tests import test_oracle_pins as pins
 
-FORWARD_PINS = [
+FORWARD_PIN_NAMES = [
     "test_inverse_worked_case_bitwise",
     "test_inverse_identity_and_library",
     "test_flat_metric_gives_zero_christoffel_and_listing1_form",
@@ -25,11 +28,25 @@ FORWARD_PINS = [
     "test_metric_compatibility",
     "test_packing_convention",
 ]
-ADJOINT_PINS = [
+ADJOINT_PIN_NAMES = [
     "test_adjoint_central_differences",
     "test_adjoint_all_outputs_and_dot_product_identity",
     "test_adjoint_against_torch_autograd",
 ]
+FORWARD_PINS = [(n, getattr(pins, n)) for n in FORWARD_PIN_NAMES]
+ADJOINT_PINS = [(n, getattr(pins, n)) for n in ADJOINT_PIN_NAMES]
+FD_PINS = ([("mode_exact_o%d_%d" % (o, f), lambda o=o, f=f, r=r: fd_pins.test_discrete_derivative_of_a_mode_is_exact(o, f, r))
+            for o in (2, 4) for f, r in ((13, 34), (4, 6 + 3 * 4))] +
+           [("convergence_o%d" % o, lambda o=o: fd_pins.test_convergence_order(o)) for o in (2, 4)] +
+           [("axis_placement", fd_pins.test_axis_placement_and_copies),
+            ("constants", fd_pins.test_constant_fields_have_zero_derivatives)])
+EXPR_PINS = [("assign_add_outer", expr_pins.test_assign_add_outer_bitwise),
+             ("einsum", expr_pins.test_contractions_against_einsum),
+             ("identity_factors", expr_pins.test_contractions_with_identity_factors_are_exact),
+             ("kij", expr_pins.test_kij),
+             ("integers_exact", expr_pins.test_sums_and_outer_products_exact_on_integers),
+             ("contractions_integers_exact", expr_pins.test_contractions_exact_on_integers),
+             ("kij_rank_one", expr_pins.test_kij_minus_lapse_term_is_rank_one)]
 
 # (id, exact text in oracle/dtg_oracle.c, replacement).  Each text occurs exactly once.
 FORWARD_MUTANTS = [
@@ -84,47 +101,85 @@ ADJOINT_MUTANTS = [
 ]
 
 
-def _build_copy(tmp_path, old, new):
-    """Compile the oracle sources with dtg_oracle.c edited (old -> new) into tmp_path; return the .so."""
+FD_MUTANTS = [
+    ("fd-o2-sign", "return (v[3] - v[1]) / (2.0 * h);", "return (v[1] - v[3]) / (2.0 * h);"),
+    ("fd-o2-factor", "return (v[3] - v[1]) / (2.0 * h);", "return (v[3] - v[1]) / h;"),
+    ("fd-o4-outer-sign", "(8.0 * (v[3] - v[1]) - (v[4] - v[0]))", "(8.0 * (v[3] - v[1]) - (v[4] + v[0]))"),
+    ("fd-o4-dropped-term", "(8.0 * (v[3] - v[1]) - (v[4] - v[0]))", "(8.0 * (v[3] - v[1]))"),
+    ("fd-o4-denominator", "/ (12.0 * h);", "/ (6.0 * h);"),
+    ("fd-spacing-of-axis-0", "deriv(in16[p], ix, iy, iz, k, nx, ny, nz, h[k], order)",
+     "deriv(in16[p], ix, iy, iz, k, nx, ny, nz, h[0], order)"),
+    ("fd-metric-axes-reversed", "deriv(in16[p], ix, iy, iz, k, nx, ny, nz, h[k], order)",
+     "deriv(in16[p], ix, iy, iz, 2 - k, nx, ny, nz, h[k], order)"),
+    ("fd-shift-transposed", "deriv(in16[13 + i], ix, iy, iz, j, nx, ny, nz, h[j], order)",
+     "deriv(in16[13 + j], ix, iy, iz, i, nx, ny, nz, h[i], order)"),
+    ("fd-K-copied-from-g", "out43[24 + p][x] = in16[6 + p][x];", "out43[24 + p][x] = in16[p][x];"),
+]
+EXPR_MUTANTS = [
+    ("eq14-dropped-operand", "const int terms = eq - 10;", "const int terms = eq == 14 ? 3 : eq - 10;"),
+    ("eq16-repeated-index", "out[9 * i + 3 * j + k][x] = (in[i][x] * in[3 + j][x]) * in[6 + k][x];",
+     "out[9 * i + 3 * j + k][x] = (in[i][x] * in[3 + j][x]) * in[6 + j][x];"),
+    ("eq17-repeated-index", "((in[i][x] * in[3 + j][x]) * in[6 + k][x]) * in[9 + l][x];",
+     "((in[i][x] * in[3 + j][x]) * in[6 + k][x]) * in[9 + k][x];"),
+    ("eq18-B-transposed", "s += in[3 * i + m][x] * in[9 + 27 * m + 9 * j + 3 * k + l][x];",
+     "s += in[3 * m + i][x] * in[9 + 27 * m + 9 * j + 3 * k + l][x];"),
+    ("eq18-dropped-term", "for (int m = 0; m < 3; ++m)\n                                s += in[3 * i + m][x]",
+     "for (int m = 0; m < 2; ++m)\n                                s += in[3 * i + m][x]"),
+    ("eq19-C-transposed", "s += (in[9 + 3 * j + nn][x] * in[3 * i + m][x]) *",
+     "s += (in[9 + 3 * nn + j][x] * in[3 * i + m][x]) *"),
+    ("eq20-E-slots-swapped", "in[27 + 27 * m + 9 * nn + 3 * o + l][x];", "in[27 + 27 * m + 9 * o + 3 * nn + l][x];"),
+    ("eq20-D-transposed", "s += ((in[18 + 3 * k + o][x] *", "s += ((in[18 + 3 * o + k][x] *"),
+    ("eq21-missing-2", "(2.0 * in[0][x]) * in[1 + expr_sym(i, j)][x]", "in[0][x] * in[1 + expr_sym(i, j)][x]"),
+    ("eq21-repeated-index", "in[7 + i][x] * in[7 + j][x];", "in[7 + i][x] * in[7 + i][x];"),
+]
+
+SOURCES = ("dtg_oracle.c", "expr_oracle.c", "fd_oracle.c")
+
+
+def _build_copy(tmp_path, source, old, new):
+    """Compile the oracle sources with `source` edited (old -> new) into tmp_path; return the .so."""
     here = os.path.dirname(os.path.abspath(oracle.__file__))
-    src = open(os.path.join(here, "dtg_oracle.c")).read()
-    if old is not None:
-        assert src.count(old) == 1, old
-        src = src.replace(old, new)
-    path = tmp_path / "dtg_oracle.c"
-    path.write_text(src)
+    paths = []
+    for name in SOURCES:
+        src = open(os.path.join(here, name)).read()
+        if name == source and old is not None:
+            assert src.count(old) == 1, old
+            src = src.replace(old, new)
+        path = tmp_path / name
+        path.write_text(src)
+        paths.append(str(path))
     so = tmp_path / "liboracle_copy.so"
     subprocess.check_call(["gcc", "-std=c99", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-                           "-o", str(so), str(path), os.path.join(here, "expr_oracle.c"),
-                           os.path.join(here, "fd_oracle.c"), "-lm"])
+                           "-o", str(so)] + paths + ["-lm"])
     return str(so)
 
 
-def _failing_pins(monkeypatch, so, names):
-    """Run the named pins with the oracle module loading `so`; return the names of those that fail."""
+def _failing_pins(monkeypatch, so, battery):
+    """Run the pins of `battery` ((name, callable) pairs) with the oracle module loading `so`; return the
+    names of those that fail."""
     monkeypatch.setattr(oracle, "_LIB", so)
     monkeypatch.setattr(oracle, "_lib", None)
     failed = []
-    for name in names:
+    for name, pin in battery:
         try:
-            getattr(pins, name)()
+            pin()
         except Exception:              # an assertion, or a value the pin cannot even process
             failed.append(name)
     return failed
 
 
 def test_unchanged_copy_passes_every_pin(tmp_path, monkeypatch):
-    so = _build_copy(tmp_path, None, None)
-    assert _failing_pins(monkeypatch, so, FORWARD_PINS + ADJOINT_PINS) == []
+    so = _build_copy(tmp_path, None, None, None)
+    assert _failing_pins(monkeypatch, so, FORWARD_PINS + ADJOINT_PINS + FD_PINS + EXPR_PINS) == []
 
 
-@pytest.mark.parametrize("name,old,new", FORWARD_MUTANTS, ids=[m[0] for m in FORWARD_MUTANTS])
-def test_forward_mistake_fails_a_forward_pin(tmp_path, monkeypatch, name, old, new):
-    so = _build_copy(tmp_path, old, new)
-    assert _failing_pins(monkeypatch, so, FORWARD_PINS), name
+CASES = ([("dtg_oracle.c", FORWARD_PINS) + m for m in FORWARD_MUTANTS] +
+         [("dtg_oracle.c", ADJOINT_PINS) + m for m in ADJOINT_MUTANTS] +
+         [("fd_oracle.c", FD_PINS) + m for m in FD_MUTANTS] +
+         [("expr_oracle.c", EXPR_PINS) + m for m in EXPR_MUTANTS])
 
 
-@pytest.mark.parametrize("name,old,new", ADJOINT_MUTANTS, ids=[m[0] for m in ADJOINT_MUTANTS])
-def test_adjoint_mistake_fails_an_adjoint_pin(tmp_path, monkeypatch, name, old, new):
-    so = _build_copy(tmp_path, old, new)
-    assert _failing_pins(monkeypatch, so, ADJOINT_PINS), name
+@pytest.mark.parametrize("source,battery,name,old,new", CASES, ids=[c[2] for c in CASES])
+def test_planted_mistake_fails_a_pin(tmp_path, monkeypatch, source, battery, name, old, new):
+    so = _build_copy(tmp_path, source, old, new)
+    assert _failing_pins(monkeypatch, so, battery), name
