@@ -14,6 +14,7 @@ import oracle
 from tests import test_expr_oracle as expr_pins
 from tests import test_fd_oracle as fd_pins
 from tests import test_oracle_pins as pins
+from tests import test_tensor_expr_oracle as interp_pins
 
 FORWARD_PIN_NAMES = [
     "test_inverse_worked_case_bitwise",
@@ -133,6 +134,24 @@ EXPR_MUTANTS = [
     ("eq21-repeated-index", "in[7 + i][x] * in[7 + j][x];", "in[7 + i][x] * in[7 + i][x];"),
 ]
 
+# The tensor-index interpreter (oracle/tensor_expr.py), the runtime generator's oracle.
+INTERP_PINS = [("chain_transcribed", lambda: interp_pins.test_chain_program_equals_chain_oracle("transcribed here")),
+               ("chain_package", lambda: interp_pins.test_chain_program_equals_chain_oracle("shipped with the package")),
+               ("expressions_bitwise", interp_pins.test_benchmark_expressions_bitwise),
+               ("listings_einsum", interp_pins.test_paper_listings_against_einsum),
+               ("declared_range_einsum", interp_pins.test_sum_over_a_declared_range_against_einsum)]
+INTERP_MUTANTS = [
+    ("interp-canonical-order", "if t[a] > t[b]:", "if t[a] < t[b]:"),
+    ("interp-minus-as-plus", '"-": lambda: a - b', '"-": lambda: a + b'),
+    ("interp-divide-as-multiply", '"/": lambda: a / b', '"/": lambda: a * b'),
+    ("interp-unary-minus-dropped", "return -self._eval(node[1], env, values)", "return self._eval(node[1], env, values)"),
+    ("interp-sum-drops-last", "for v in range(self._dim_of(node[2], letter)):",
+     "for v in range(self._dim_of(node[2], letter) - 1):"),
+    ("interp-sum-ignores-range", "return self.ranges.get(letter, decl.dims[s])", "return decl.dims[s]"),
+    ("interp-offset-dropped", "env[ix[1]] + ix[2] for ix in node[2])", "env[ix[1]] for ix in node[2])"),
+    ("interp-last-assignment-wins", "if tup not in new:", "if True:"),
+]
+
 SOURCES = ("dtg_oracle.c", "expr_oracle.c", "fd_oracle.c")
 
 
@@ -171,6 +190,8 @@ def _failing_pins(monkeypatch, so, battery):
 def test_unchanged_copy_passes_every_pin(tmp_path, monkeypatch):
     so = _build_copy(tmp_path, None, None, None)
     assert _failing_pins(monkeypatch, so, FORWARD_PINS + ADJOINT_PINS + FD_PINS + EXPR_PINS) == []
+    monkeypatch.setattr(interp_pins, "Program", _load_interpreter_copy(tmp_path, None, None).Program)
+    assert _failing_pins(monkeypatch, so, INTERP_PINS) == []
 
 
 CASES = ([("dtg_oracle.c", FORWARD_PINS) + m for m in FORWARD_MUTANTS] +
@@ -183,3 +204,31 @@ CASES = ([("dtg_oracle.c", FORWARD_PINS) + m for m in FORWARD_MUTANTS] +
 def test_planted_mistake_fails_a_pin(tmp_path, monkeypatch, source, battery, name, old, new):
     so = _build_copy(tmp_path, source, old, new)
     assert _failing_pins(monkeypatch, so, battery), name
+
+
+def _load_interpreter_copy(tmp_path, old, new):
+    """Import a copy of oracle/tensor_expr.py with old -> new applied, as a module of its own."""
+    import importlib.util
+    here = os.path.dirname(os.path.abspath(oracle.__file__))
+    src = open(os.path.join(here, "tensor_expr.py")).read()
+    if old is not None:
+        assert src.count(old) == 1, old
+        src = src.replace(old, new)
+    path = tmp_path / "tensor_expr_copy.py"
+    path.write_text(src)
+    spec = importlib.util.spec_from_file_location("tensor_expr_copy_%d" % abs(hash(str(path))), str(path))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+@pytest.mark.parametrize("name,old,new", INTERP_MUTANTS, ids=[m[0] for m in INTERP_MUTANTS])
+def test_planted_interpreter_mistake_fails_a_pin(tmp_path, monkeypatch, name, old, new):
+    monkeypatch.setattr(interp_pins, "Program", _load_interpreter_copy(tmp_path, old, new).Program)
+    failed = []
+    for pin_name, pin in INTERP_PINS:
+        try:
+            pin()
+        except Exception:
+            failed.append(pin_name)
+    assert failed, name

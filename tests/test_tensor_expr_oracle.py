@@ -84,3 +84,15 @@ def test_paper_listings_against_einsum():
     # D(i,0), i = 0..2 (spatial), land on the stored elements (0,0), (0,1), (0,2) of the symmetric D
     assert np.abs(y[0:3] - ref).max() <= 1e-14
     assert np.array_equal(y[3], E[0, 0])         # D(3,0) = D(0,3)
+
+
+def test_sum_over_a_declared_range_against_einsum():
+    """A contraction letter with its own range and an offset: the spatial part (slots 1..3) of a
+    4-dimensional index, v_a = sum_{m<3} E_a,m+1 F_m+1."""
+    n = 40
+    rng = np.random.default_rng(5)
+    p = Program("index m(3); in E(4,4); in F(4); out v(4); v(a) = Sum(m, E(a,m+1)*F(m+1));")
+    E, F = rng.normal(size=(4, 4, n)), rng.normal(size=(4, n))
+    y = p.run(np.concatenate([E.reshape(16, n), F]))
+    ref = np.einsum("amx,mx->ax", E[:, 1:4], F[1:4])
+    assert np.abs(y - ref).max() <= 1e-14
