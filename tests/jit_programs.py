@@ -20,6 +20,7 @@ PROGRAMS = {
                  "D(2,3) = E(0,0); D(3,3) = E(0,0);",
     "trace_div": "in B(3,3); in s; out t; out u(3); t = Sum(i, B(i,i)); u(i) = B(i,0) / (s*s + 1);",
     "spatial_slice": "in psi(4,4) sym(0,1); out g(3,3) sym(0,1); out beta(3); g(i,j) = psi(i+1,j+1); beta(i) = psi(i+1,0);",
+    "spatial_contraction": "index m(3); in E(4,4); in F(4); out v(4); v(a) = Sum(m, E(a,m+1)*F(m+1));",
 }
 
 BAD = {
