@@ -219,7 +219,7 @@ TL_API tl_status tl_jit_launch(tl_jit_kernel *kernel, const double *const *in, d
                                tl_stream stream);
 TL_API void tl_jit_destroy(tl_jit_kernel *kernel);
 
-TL_API /*
+/*
  * The forward chain with the spatial derivatives formed on the grid instead of read: d_k g_ij and
  * d_j beta_i by centred finite differences of order 2 or 4 on a periodic nx x ny x nz grid (x fastest:
  * point (ix, iy, iz) is element ix + nx (iy + ny iz) of every array), spacings hx, hy, hz.  The paper
