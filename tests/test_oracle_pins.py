@@ -271,15 +271,22 @@ def test_killing_field_rotation():
     assert np.abs(dtg - (-2 * alpha * K)).max() <= 1e-13
 
 
-def test_shift_derivative_and_eq5_from_the_lie_derivative():
+@pytest.mark.parametrize("seed,stretch", [(17, 1.0), (18, 1.0), (19, 25.0)])
+def test_shift_derivative_and_eq5_from_the_lie_derivative(seed, stretch):
     """Christoffel-free closed forms on a generic curved grid.  With the vector beta^k = g^kl beta_l,
     the symmetric part of nabla_j beta_i is half the Lie derivative of the metric along beta^k,
         L_beta g_ij = beta^k d_k g_ij + g_kj d_i beta^k + g_ik d_j beta^k,
     with d_i beta^k = -g^ka (d_i g_ab) g^bl beta_l + g^kl d_i beta_l, and its antisymmetric part is that
     of d_j beta_i (Gamma^k_ij is symmetric in ij).  So nabla_j beta_i = L_ij / 2 + (d_j beta_i -
-    d_i beta_j) / 2 and Eq. 5 gives d_t g_ij = -2 alpha K_ij + L_ij.  The inverse here is numpy's."""
-    x = gridgen.random_grid(4096, 17)
+    d_i beta_j) / 2 and Eq. 5 gives d_t g_ij = -2 alpha K_ij + L_ij.  The inverse here is numpy's.
+    stretch > 1 scales the metric's z row and column (and their derivatives) into a stretched,
+    anisotropic metric with condition number ~stretch^2."""
+    x = gridgen.random_grid(4096, seed)
     G, D, K, alpha, beta, B = unpack_inputs(x)
+    s3 = np.array([1.0, 1.0, stretch])
+    G = G * s3[:, None, None] * s3[None, :, None]
+    D = D * s3[:, None, None, None] * s3[None, :, None, None]
+    x = pack_inputs(G, D, K, alpha, beta, B)
     H = np.linalg.inv(G.transpose(2, 0, 1)).transpose(1, 2, 0)
     bu = np.einsum("kln,ln->kn", H, beta)
     dbu = -np.einsum("kan,abin,bln,ln->kin", H, D, H, beta) + np.einsum("kln,lin->kin", H, B)
