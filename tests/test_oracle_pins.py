@@ -327,6 +327,16 @@ def test_packing_convention():
                 assert abs(y[6 + 6 * i + P[(j, k)], 0] - ref) <= 1e-15
 
 
+@pytest.mark.parametrize("n,threads", [(10007, 4), (5, 8), (1, 3)])
+def test_threaded_forward_is_the_same_loop(n, threads):
+    """The host-thread split the CPU baseline times (disjoint point ranges, the C loop unchanged on
+    each) gives the single call's outputs bit for bit, including ranges left empty."""
+    x = gridgen.random_grid(n, 23)
+    out = np.full((39, n), np.nan)
+    oracle.forward_threaded(x, out, threads)
+    assert np.array_equal(out, oracle.forward(x))
+
+
 def test_argument_errors_and_empty():
     assert oracle.forward(np.zeros((43, 0))).shape == (39, 0)
     with pytest.raises(AssertionError):
