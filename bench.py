@@ -190,6 +190,25 @@ def time_oracle(x_host, budget_s=10.0, max_s=30.0):
     return points / el, threads, "%d pass(es) of the oracle over %d points of the workload grid, %.1f s" % (reps, n, el)
 
 
+def time_oracle_single(x_host, budget_s=3.0, n_max=1 << 18):
+    """The same oracle loop on ONE host thread (no split), over the first n_max points of the workload
+    grid, repeated until ~budget_s.  Returns (points/s, sample description)."""
+    import numpy as np
+    import oracle
+    x = np.ascontiguousarray(x_host[:, :n_max])
+    n = x.shape[1]
+    out = np.empty((39, n), dtype=np.float64)
+    reps = 0
+    t0 = time.perf_counter()
+    while True:
+        oracle.forward_threaded(x, out, 1)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s:
+            break
+    return reps * n / el, "%d pass(es) over the first %d points of the workload grid, one thread, %.1f s" % (reps, n, el)
+
+
 def reference_arm(args):
     """The oracle (plain CPU loop nest) as the reference implementation, on this host's cores."""
     import numpy as np
@@ -275,6 +294,44 @@ def cuda_time(fn, steps, stream, warmup=3):
     e1.record(stream)
     torch.cuda.synchronize()
     return e0.elapsed_time(e1) / steps
+
+
+def small_grid(dev, stream):
+    """One small grid (N = 4096, seed 0; inputs + outputs 2.7 MB, resident in L2): launch-bound, so
+    microseconds per launch, warm (inputs in L2 from the previous launch) and cold (a 256 MB write,
+    twice the L2, before every launch).  Every launch is enqueued behind a fixed-length GPU spin, so
+    the GPU runs them back to back and the events around each launch time the kernel, not the host's
+    enqueue rate."""
+    import torch
+    import gridgen
+    import paper_1804_10120_gb300 as tl
+    n0 = 4096
+    x0 = torch.from_numpy(gridgen.random_grid(n0, 0)).to(dev)
+    y0 = torch.empty((39, n0), dtype=torch.float64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    reps = 21
+
+    def per_launch_us(cold):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * reps)]
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            torch.cuda._sleep(50_000_000)       # ~25-50 ms of clock cycles: time to enqueue what follows
+            for i in range(reps):
+                if cold:
+                    flush.fill_(i & 0xff)
+                ev[2 * i].record(stream)
+                tl.tl_dtg_forward(x0, y0, stream=stream)
+                ev[2 * i + 1].record(stream)
+        torch.cuda.synchronize()
+        return sorted(1e3 * ev[2 * i].elapsed_time(ev[2 * i + 1]) for i in range(1, reps))
+
+    tl.tl_dtg_forward(x0, y0, stream=stream)
+    warm, cold = per_launch_us(False), per_launch_us(True)
+    return {"workload": "single grid N=4096, seed 0 (2.7 MB: fits in L2); launch-bound, microseconds per launch",
+            "us_warm_median": warm[len(warm) // 2], "us_cold_median": cold[len(cold) // 2],
+            "us_cold_min": cold[0], "us_cold_max": cold[-1],
+            "method": "20 launches queued behind a GPU spin, events around each; cold: 256 MB written on "
+                      "the launching stream before each launch"}
 
 
 def extras(dev, stream, steps, x64, hbm):
@@ -405,6 +462,10 @@ def extras(dev, stream, steps, x64, hbm):
                   "arrays_GB_s": round(r["arrays_GB_s"], 1), "fused_graph_GB_s": round(r["fused_graph_GB_s"], 1),
                   "arrays_graph_GB_s": round(r["arrays_graph_GB_s"], 1), "arrays_launches": r["arrays_launches"]}
                  for r in rows]}
+    try:
+        out["small_grid"] = small_grid(dev, stream)
+    except Exception as e:      # context for the small case; never blocks the bench line
+        out["small_grid"] = {"unavailable": repr(e)[:200]}
     return out
 
 
@@ -641,6 +702,11 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu:
         v, cores, sample = time_oracle(x_host)
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+        try:
+            v1, sample1 = time_oracle_single(x_host)
+            cpu["single_thread"] = {"value": v1, "unit": UNIT, "cores": 1, "sample": sample1}
+        except Exception as e:     # the all-core figure above is the baseline; this one is context
+            cpu["single_thread"] = {"unavailable": repr(e)[:200]}
 
     if rank == 0:
         line = {
