@@ -97,6 +97,17 @@ TL_API tl_status tl_dtg_backward(const tl_dtg_in *in, const tl_dtg_gout *gout, c
                           tl_dtype dtype, tl_stream stream);
 
 /*
+ * Forward and adjoint in one pass, for a functional whose upstream gradients are known before the forward
+ * runs (L = sum gout * out with gout given up front, e.g. a loss linear in the outputs): writes the 39
+ * outputs exactly as tl_dtg_forward does (bit for bit) and the 43 input gradients as tl_dtg_backward
+ * does (same definition; rounding may differ in the last bits), reading every input once.  g^ij, the
+ * Eq. 6 bracket and Gamma are formed once and serve both.  TL_F64 only (TL_ERR_UNSUPPORTED otherwise).
+ * Same rules as tl_dtg_forward and tl_dtg_backward; out and gin must not overlap each other, in or gout.
+ */
+TL_API tl_status tl_dtg_forward_backward(const tl_dtg_in *in, const tl_dtg_out *out, const tl_dtg_gout *gout,
+                                         const tl_dtg_gin *gin, int64_t n, tl_dtype dtype, tl_stream stream);
+
+/*
  * Forward with HOST arrays (end-to-end form): copies the 43 input arrays host->device into `workspace`,
  * runs the forward kernel there and copies the 39 outputs device->host.  The work is cut into chunks of
  * 2^19 points that flow through three library-owned streams (host->device copies, kernel,

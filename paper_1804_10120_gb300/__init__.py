@@ -52,10 +52,11 @@ def lib():
             vp, i64, i32, sz = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_size_t
             L.tl_dtg_forward.argtypes = [vp, vp, i64, i32, vp]
             L.tl_dtg_backward.argtypes = [vp, vp, vp, i64, i32, vp]
+            L.tl_dtg_forward_backward.argtypes = [vp, vp, vp, vp, i64, i32, vp]
             L.tl_dtg_forward_host.argtypes = [vp, vp, i64, i32, vp, sz, vp]
             L.tl_dtg_host_workspace_bytes.argtypes = [i64, i32]
             L.tl_dtg_host_workspace_bytes.restype = sz
-            for f in (L.tl_dtg_forward, L.tl_dtg_backward, L.tl_dtg_forward_host):
+            for f in (L.tl_dtg_forward, L.tl_dtg_backward, L.tl_dtg_forward_backward, L.tl_dtg_forward_host):
                 f.restype = i32
             L.tl_status_string.argtypes = [i32]
             L.tl_status_string.restype = ctypes.c_char_p
@@ -170,6 +171,35 @@ def tl_dtg_backward(inputs, gout, gin=None, dtype="f64", stream=None):
         _check(lib().tl_dtg_backward(ctypes.byref(itab), ctypes.byref(gtab), ctypes.byref(gitab), n, code,
                                      _stream_handle(stream, dev)))
     return gin
+
+
+def tl_dtg_forward_backward(inputs, gout, outputs=None, gin=None, dtype="f64", stream=None):
+    """Forward and adjoint in one launch for upstream gradients known up front (gout: [39, n] or 39
+    arrays, None = output not in the functional).  Returns (outputs [39, n], gin [43, n]), allocated
+    where not given."""
+    import torch
+    code = _dtype_code(dtype)
+    td = _torch_dtype(code)
+    rows = _rows(inputs, N_IN, "inputs")
+    n = rows[0].shape[0]
+    dev = rows[0].device
+    grows = _rows(gout, N_OUT, "gout", allow_none=True)
+    if outputs is None:
+        outputs = torch.empty((N_OUT, n), dtype=td, device=dev)
+    if gin is None:
+        gin = torch.empty((N_IN, n), dtype=td, device=dev)
+    itab = _table(rows, N_IN, n, td, "cuda", "inputs")
+    otab = _table(_rows(outputs, N_OUT, "outputs"), N_OUT, n, td, "cuda", "outputs")
+    gtab = _table(grows, N_OUT, n, td, "cuda", "gout")
+    gitab = _table(_rows(gin, N_IN, "gin"), N_IN, n, td, "cuda", "gin")
+    if n == 0:
+        _nonnull_empty(itab, N_IN)
+        _nonnull_empty(otab, N_OUT)
+        _nonnull_empty(gitab, N_IN)
+    with torch.cuda.device(dev):
+        _check(lib().tl_dtg_forward_backward(ctypes.byref(itab), ctypes.byref(otab), ctypes.byref(gtab),
+                                             ctypes.byref(gitab), n, code, _stream_handle(stream, dev)))
+    return outputs, gin
 
 
 def tl_wait_timeouts():

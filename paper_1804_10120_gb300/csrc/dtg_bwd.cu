@@ -10,27 +10,22 @@
 //   dbetabar_ij = Nbar_ij,  S_p = Nbar_ij + Nbar_ji (i<j) or Nbar_ii,
 //   betabar_k = -sum_p S_p Gamma^k_p = -sum_l h_kl u_l,  u_l = sum_p S_p T_lp
 //   Gammabar_kp = V_kp - beta_k S_p
-//   Hbar_il = 1/2 sum_p Gammabar_ip T_lp (+ the g^ij upstream gradient on the stored entries)
 //   Tbar_lp = sum_i h_il Gammabar_ip, scattered through the bracket's three terms onto d_k g_ij
-//   gbar_ij (i<j) = -(H A H)_ij, gbar_ii = -(H A H)_ii / 2 with A = Hbar + Hbar^T   (from dH = -H dG H)
-// where W, V, U are the upstream gradients of d_t g, Gamma and nabla beta.
-#include "dtg_fwd_body.cuh"
+//   P = Tbar T^T (+ h A_Y),  gbar_ii = -(P H)_ii,  gbar_ij = -((P H)_ij + (P H)_ji)   (i < j)
+// where W, V, U, Y are the upstream gradients of d_t g, Gamma, nabla beta and g^ij (the last line is
+// -H A H folded onto the stored pairs, A = Hbar + Hbar^T; dtg_bwd_body.cuh derives it).
+#include "dtg_bwd_body.cuh"
 #include "ff.cuh"
 #include "tl_kernels.h"
 
 namespace tl {
 
-template <typename T> __device__ __forceinline__ T ld_opt(const T *p, int64_t x)
-{
-    return p ? ld_stream(p + x) : T(0);
-}
-
-// kU: upstream gradient of nabla beta present; kG: upstream gradient of g^ij present.  kIntMul: the 68
+// kU: upstream gradient of nabla beta present; kG: upstream gradient of g^ij present.  kIntMul: the 59
 // products not fused into an FMA run on the integer pipes (mul_int, the same bits as the FP64 multiply).
 template <bool kU, bool kG, bool kIntMul = true>
 __device__ __forceinline__ void bwd_point_f64(const BwdArgs<double> &a, int64_t x)
 {
-    // ---- recompute: inverse metric, bracket, Christoffel symbols
+    // ---- recompute: inverse metric and bracket
     const double g00 = ld_stream(a.in[IN_G + 0] + x), g01 = ld_stream(a.in[IN_G + 1] + x),
                  g02 = ld_stream(a.in[IN_G + 2] + x), g11 = ld_stream(a.in[IN_G + 3] + x),
                  g12 = ld_stream(a.in[IN_G + 4] + x), g22 = ld_stream(a.in[IN_G + 5] + x);
@@ -58,45 +53,15 @@ __device__ __forceinline__ void bwd_point_f64(const BwdArgs<double> &a, int64_t 
     double T[3][6];
     christoffel_bracket<double>(dg, T);
 
-    // ---- Eq. 5
-    const double alpha = ld_stream(a.in[IN_ALPHA] + x);
-    const double m2a = -twice_exact(alpha);
-    double W[6];
-    double asum = 0.0;
+    // ---- Eq. 5 and the footnote, reversed
+    double W[6], K[6], S[6];
 #pragma unroll
     for (int p = 0; p < 6; ++p) {
         W[p] = ld_opt(a.gout[OUT_DTG + p], x);
-        const double K = ld_stream(a.in[IN_K + p] + x);
-        st_stream(a.gin[IN_K + p] + x, mul64<kIntMul>(m2a, W[p]));
-        asum = (p == 0) ? mul64<kIntMul>(K, W[p]) : fma(K, W[p], asum);
+        K[p] = ld_stream(a.in[IN_K + p] + x);
     }
-    st_stream(a.gin[IN_ALPHA] + x, -twice_exact(asum));
+    adj_eq5_footnote<kU, kIntMul>(a, x, W, K, ld_stream(a.in[IN_ALPHA] + x), S);
 
-    // ---- covariant derivative of the shift: Nbar = dbetabar, S (symmetric fold of Nbar)
-    double S[6];
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            const int p = sym(i, j);
-            double nbar = (i == j) ? twice_exact(W[p]) : W[p];
-            if (kU)
-                nbar += ld_opt(a.gout[OUT_DBCOV + 3 * i + j], x);
-            st_stream(a.gin[IN_DBETA + 3 * i + j] + x, nbar);
-            if (kU) {
-                if (i == j)
-                    S[p] = nbar;
-                else if (i < j)
-                    S[p] = nbar;
-                else
-                    S[p] += nbar;
-            }
-        }
-    if (!kU) {
-#pragma unroll
-        for (int p = 0; p < 6; ++p)
-            S[p] = twice_exact(W[p]);
-    }
     // betabar_k = -sum_p S_p Gamma^k_p = -sum_l h_kl u_l with u_l = sum_p S_p T_lp: Gamma itself is
     // never needed by the adjoint
     double u[3], beta[3];
@@ -123,86 +88,35 @@ __device__ __forceinline__ void bwd_point_f64(const BwdArgs<double> &a, int64_t 
         for (int p = 0; p < 6; ++p)
             gbar[k][p] = fma(-beta[k], S[p], ld_opt(a.gout[OUT_GAMMA + 6 * k + p], x));
 
-    // ---- Eq. 6: Hbar (not symmetric) and Tbar
-    double Hb[3][3];
+    // ---- Eq. 6: Tbar, scattered onto d_k g_ij
+    double Tb[3][6];
+    adj_tbar<kIntMul>(h, gbar, Tb);
+    adj_bracket_store(a, x, Tb);
+
+    // ---- inverse: P = Tbar T^T (= H Hbar), plus h A_Y; gbar = -fold(P H)
+    double P[3][3];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
         for (int l = 0; l < 3; ++l) {
-            double s = mul64<kIntMul>(gbar[i][0], T[l][0]);
+            double s = mul64<kIntMul>(Tb[i][0], T[l][0]);
 #pragma unroll
             for (int p = 1; p < 6; ++p)
-                s = fma(gbar[i][p], T[l][p], s);
-            Hb[i][l] = half_exact(s);
+                s = fma(Tb[i][p], T[l][p], s);
+            P[i][l] = s;
         }
-    double Tb[3][6];
-#pragma unroll
-    for (int l = 0; l < 3; ++l)
+    if (kG) {
+        double Y[6];
 #pragma unroll
         for (int p = 0; p < 6; ++p)
-            Tb[l][p] = fma(h[sym(2, l)], gbar[2][p],
-                           fma(h[sym(1, l)], gbar[1][p], mul64<kIntMul>(h[sym(0, l)], gbar[0][p])));
-
-    // ---- bracket -> d_k g_ij: every T_lp term of Eq. 6 scattered onto the stored derivative it reads.
-    // The first contribution to an entry is assigned rather than added to zero (an FP64 add saved per
-    // entry; `seen` is resolved at compile time once the loops are unrolled).
-    double dgb[18];
-    bool seen[18] = {};
-    auto put = [&](int s, double t) {
-        dgb[s] = seen[s] ? dgb[s] + t : t;
-        seen[s] = true;
-    };
+            Y[p] = ld_opt(a.gout[OUT_GINV + p], x);
+        adj_add_hAY<kIntMul>(h, Y, P);
+    }
+    double F[6];
+    adj_fold_PH<kIntMul>(P, H, F);
 #pragma unroll
-    for (int l = 0; l < 3; ++l)
-#pragma unroll
-        for (int j = 0; j < 3; ++j)
-#pragma unroll
-            for (int k = j; k < 3; ++k) {
-                const double t = Tb[l][sym(j, k)];
-                if (l == j) {                       // T = d_k g_jj
-                    put(3 * sym(j, j) + k, t);
-                } else if (l == k) {                // T = d_j g_kk
-                    put(3 * sym(k, k) + j, t);
-                } else if (j == k) {                // T = 2 d_j g_jl - d_l g_jj
-                    put(3 * sym(j, l) + j, twice_exact(t));
-                    put(3 * sym(j, j) + l, -t);
-                } else {                            // T = d_k g_jl + d_j g_lk - d_l g_jk
-                    put(3 * sym(j, l) + k, t);
-                    put(3 * sym(l, k) + j, t);
-                    put(3 * sym(j, k) + l, -t);
-                }
-            }
-#pragma unroll
-    for (int s = 0; s < 18; ++s)
-        st_stream(a.gin[IN_DG + s] + x, dgb[s]);
-
-    // ---- inverse: gbar = fold of -H Hbar H onto the stored pairs, via A = Hbar + Hbar^T
-    double A[6];
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = i; j < 3; ++j) {
-            double v = (i == j) ? twice_exact(Hb[i][i]) : Hb[i][j] + Hb[j][i];
-            if (kG) {
-                const double wg = ld_opt(a.gout[OUT_GINV + sym(i, j)], x);
-                v += (i == j) ? twice_exact(wg) : wg;   // the stored g^ij entry enters Hbar once
-            }
-            A[sym(i, j)] = v;
-        }
-    double M[3][3];                                   // M = H A
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j)
-            M[i][j] = fma(H[sym(i, 2)], A[sym(2, j)],
-                          fma(H[sym(i, 1)], A[sym(1, j)], mul64<kIntMul>(H[sym(i, 0)], A[sym(0, j)])));
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = i; j < 3; ++j) {
-            const double v = fma(M[i][2], H[sym(2, j)], fma(M[i][1], H[sym(1, j)], mul64<kIntMul>(M[i][0], H[sym(0, j)])));
-            st_stream(a.gin[IN_G + sym(i, j)] + x, (i == j) ? -half_exact(v) : -v);
-        }
+    for (int p = 0; p < 6; ++p)
+        st_stream(a.gin[IN_G + p] + x, neg_exact(F[p]));
 }
 
 // ------------------------------------------------------------------------------ float-float adjoint
@@ -469,31 +383,31 @@ static bool any_present(const double *const *p, int count)
 
 // The upstream gradients of nabla beta and g^ij are often absent altogether; kernels specialised on
 // their presence skip that work.  Within a group, NULL entries read as zero.
-cudaError_t launch_bwd_f64(const BwdArgs<double> &a, int64_t n, int grid, cudaStream_t s)
+cudaError_t launch_bwd_f64(const BwdArgs<double> &a, int64_t n, LaunchShape sh, cudaStream_t s)
 {
     const bool hasU = any_present(a.gout + OUT_DBCOV, 9), hasG = any_present(a.gout + OUT_GINV, 6);
     if (hasU && hasG)
-        dtg_bwd_f64_kernel<true, true><<<grid, kBwdThreads, 0, s>>>(a, n);
+        dtg_bwd_f64_kernel<true, true><<<sh.grid, sh.threads, 0, s>>>(a, n);
     else if (hasU)
-        dtg_bwd_f64_kernel<true, false><<<grid, kBwdThreads, 0, s>>>(a, n);
+        dtg_bwd_f64_kernel<true, false><<<sh.grid, sh.threads, 0, s>>>(a, n);
     else if (hasG)
-        dtg_bwd_f64_kernel<false, true><<<grid, kBwdThreads, 0, s>>>(a, n);
+        dtg_bwd_f64_kernel<false, true><<<sh.grid, sh.threads, 0, s>>>(a, n);
     else
-        dtg_bwd_f64_kernel<false, false><<<grid, kBwdThreads, 0, s>>>(a, n);
+        dtg_bwd_f64_kernel<false, false><<<sh.grid, sh.threads, 0, s>>>(a, n);
     return cudaGetLastError();
 }
 
-cudaError_t launch_bwd_ff(const BwdArgs<double> &a, int64_t n, int grid, cudaStream_t s)
+cudaError_t launch_bwd_ff(const BwdArgs<double> &a, int64_t n, LaunchShape sh, cudaStream_t s)
 {
     const bool hasU = any_present(a.gout + OUT_DBCOV, 9), hasG = any_present(a.gout + OUT_GINV, 6);
     if (hasU && hasG)
-        dtg_bwd_ff_kernel<true, true><<<grid, kBwdFfThreads, 0, s>>>(a, n);
+        dtg_bwd_ff_kernel<true, true><<<sh.grid, sh.threads, 0, s>>>(a, n);
     else if (hasU)
-        dtg_bwd_ff_kernel<true, false><<<grid, kBwdFfThreads, 0, s>>>(a, n);
+        dtg_bwd_ff_kernel<true, false><<<sh.grid, sh.threads, 0, s>>>(a, n);
     else if (hasG)
-        dtg_bwd_ff_kernel<false, true><<<grid, kBwdFfThreads, 0, s>>>(a, n);
+        dtg_bwd_ff_kernel<false, true><<<sh.grid, sh.threads, 0, s>>>(a, n);
     else
-        dtg_bwd_ff_kernel<false, false><<<grid, kBwdFfThreads, 0, s>>>(a, n);
+        dtg_bwd_ff_kernel<false, false><<<sh.grid, sh.threads, 0, s>>>(a, n);
     return cudaGetLastError();
 }
 

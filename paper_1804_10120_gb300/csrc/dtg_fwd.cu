@@ -285,19 +285,19 @@ cudaError_t occupancy_batched(int dtype, int threads, int *blocks)
 }
 
 // ------------------------------------------------------------------------------------------- launchers
-cudaError_t launch_fwd_f64(const FwdArgs<double> &a, int64_t n, int grid, cudaStream_t s)
+cudaError_t launch_fwd_f64(const FwdArgs<double> &a, int64_t n, LaunchShape sh, cudaStream_t s)
 {
-    dtg_fwd_f64_kernel<<<grid, kFwdThreads, 0, s>>>(a, n);
+    dtg_fwd_f64_kernel<<<sh.grid, sh.threads, 0, s>>>(a, n);
     return cudaGetLastError();
 }
 
-cudaError_t launch_fwd_f32(const FwdArgs<float> &a, int64_t n, int grid, cudaStream_t s)
+cudaError_t launch_fwd_f32(const FwdArgs<float> &a, int64_t n, LaunchShape sh, cudaStream_t s)
 {
-    dtg_fwd_f32_kernel<<<grid, kFwdThreads, 0, s>>>(a, n);
+    dtg_fwd_f32_kernel<<<sh.grid, sh.threads, 0, s>>>(a, n);
     return cudaGetLastError();
 }
 
-cudaError_t launch_fwd_f32_staged(const FwdArgs<float> &a, int64_t n, int sms, int tail_grid, cudaStream_t s)
+cudaError_t launch_fwd_f32_staged(const FwdArgs<float> &a, int64_t n, int sms, LaunchShape tail, cudaStream_t s)
 {
     constexpr int kTile = kF32StagedTile;
     bool aligned = true;
@@ -315,7 +315,11 @@ cudaError_t launch_fwd_f32_staged(const FwdArgs<float> &a, int64_t n, int sms, i
         t.in[k] += done;
     for (int k = 0; k < N_OUT; ++k)
         t.out[k] += done;
-    return launch_fwd_f32(t, n - done, (int)std::min<int64_t>(tail_grid, (n - done + kFwdThreads - 1) / kFwdThreads), s);
+    // the tail is at most kF32StagedTile - 1 points, or the whole grid when the inputs are not aligned
+    const int64_t m = n - done;
+    if (ntiles > 0)
+        tail = LaunchShape{(int)((m + kFwdThreads - 1) / kFwdThreads), kFwdThreads};
+    return launch_fwd_f32(t, m, tail, s);
 }
 
 cudaError_t occupancy_fwd(int *f64, int *f32, int *ff)

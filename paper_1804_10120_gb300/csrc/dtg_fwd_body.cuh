@@ -47,14 +47,22 @@ template <bool kIntMul> __device__ __forceinline__ double mul64(double a, double
     return kIntMul ? mul_int(a, b) : a * b;
 }
 
+// Intermediates of the binary64 chain at one point that the fused forward + adjoint kernel reuses:
+// g^ij, 1/2 g^ij, the Eq. 6 bracket and Gamma (packed as in the output table).
+struct ChainF64Keep {
+    double ginv[6], h[6], T[3][6], gam[3][6];
+};
+
 // The chain on one point's 43 input values (already in registers, in the input-table order); the 39
-// outputs go to o.out[s][x] (o: any argument block with an `out` table).  kScaled: the d_k g_ij and
-// d_j beta_i entries of v are differences that still need one common factor sd (a finite-difference
-// stencil on a grid with equal spacings); sd is then applied once to 1/2 g^il and fused into
-// nabla_j beta_i instead of to each of the 27 derivatives.  kIntMul: the 37 products that are not
-// fused into an FMA go to the integer pipes (mul_int); the results are the same bits either way.
+// outputs go to o.out[s][x] (o: any argument block with an `out` table) and the intermediates to k.
+// kScaled: the d_k g_ij and d_j beta_i entries of v are differences that still need one common factor
+// sd (a finite-difference stencil on a grid with equal spacings); sd is then applied once to
+// 1/2 g^il and fused into nabla_j beta_i instead of to each of the 27 derivatives.  kIntMul: the 37
+// products that are not fused into an FMA go to the integer pipes (mul_int); the results are the same
+// bits either way.
 template <class OutTable, bool kScaled = false, bool kIntMul = true>
-__device__ __forceinline__ void chain_f64(const double (&v)[N_IN], const OutTable &o, int64_t x, double sd = 1.0)
+__device__ __forceinline__ void chain_f64_keep(const double (&v)[N_IN], const OutTable &o, int64_t x, double sd,
+                                               ChainF64Keep &k)
 {
     // step 1: inverse metric by cofactors; det by first-row expansion
     const double g00 = v[IN_G + 0], g01 = v[IN_G + 1],
@@ -83,6 +91,8 @@ __device__ __forceinline__ void chain_f64(const double (&v)[N_IN], const OutTabl
         else
             h[p] = half_exact(ginv[p]);      // 1/2 g^il of Eq. 6
         st_stream(o.out[OUT_GINV + p] + x, ginv[p]);
+        k.ginv[p] = ginv[p];
+        k.h[p] = h[p];
     }
 
     // step 2: Christoffel symbols, Eq. 6
@@ -95,6 +105,8 @@ __device__ __forceinline__ void chain_f64(const double (&v)[N_IN], const OutTabl
         for (int p = 0; p < 6; ++p) {
             gam[i][p] = fma(h[sym(i, 2)], T[2][p], fma(h[sym(i, 1)], T[1][p], mul64<kIntMul>(h[sym(i, 0)], T[0][p])));
             st_stream(o.out[OUT_GAMMA + 6 * i + p] + x, gam[i][p]);
+            k.T[i][p] = T[i][p];
+            k.gam[i][p] = gam[i][p];
         }
 
     // step 3: nabla_j beta_i = d_j beta_i - Gamma^k_ij beta_k.  Gamma^k_ij beta_k is symmetric in ij, so
@@ -130,6 +142,14 @@ __device__ __forceinline__ void chain_f64(const double (&v)[N_IN], const OutTabl
             const double s = (i == j) ? twice_exact(nb[i][i]) : nb[i][j] + nb[j][i];
             st_stream(o.out[OUT_DTG + p] + x, fma(m2a, K, s));
         }
+}
+
+// The chain alone (the intermediates are dropped; the compiler removes the copies).
+template <class OutTable, bool kScaled = false, bool kIntMul = true>
+__device__ __forceinline__ void chain_f64(const double (&v)[N_IN], const OutTable &o, int64_t x, double sd = 1.0)
+{
+    ChainF64Keep unused;
+    chain_f64_keep<OutTable, kScaled, kIntMul>(v, o, x, sd, unused);
 }
 
 template <bool kIntMul = true> __device__ __forceinline__ void fwd_point_f64(const FwdArgs<double> &a, int64_t x)

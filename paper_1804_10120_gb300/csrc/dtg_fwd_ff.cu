@@ -47,9 +47,9 @@ __global__ void __launch_bounds__(kFwdThreads, 2) dtg_fwd_ff_kernel(const FwdArg
     }
 }
 
-cudaError_t launch_fwd_ff(const FwdArgs<double> &a, int64_t n, int grid, cudaStream_t s)
+cudaError_t launch_fwd_ff(const FwdArgs<double> &a, int64_t n, LaunchShape sh, cudaStream_t s)
 {
-    dtg_fwd_ff_kernel<<<grid, kFwdThreads, 0, s>>>(a, n);
+    dtg_fwd_ff_kernel<<<sh.grid, sh.threads, 0, s>>>(a, n);
     return cudaGetLastError();
 }
 
@@ -135,6 +135,8 @@ __global__ void f64_int_testing_kernel(int op, const double *a, const double *b,
     for (int64_t i = gs.first; i < n; i += gs.step) {
         if (op == 0)
             y[i] = mul_int(a[i], b[i]);
+        else if (op == 1)
+            y[i] = rcp_f64(a[i]);
         else
             y[i] = fma(a[i], b[i], c[i]);
     }
@@ -145,7 +147,7 @@ __global__ void f64_int_testing_kernel(int op, const double *a, const double *b,
 extern "C" TL_API tl_status tl_testing_f64_int(int op, const double *a, const double *b, const double *c, double *y,
                                                int64_t n, tl_stream stream)
 {
-    if (op < 0 || op > 3 || op == 1 || op == 2 || n < 0 || !a || !b || !y || (op == 3 && !c))
+    if (op < 0 || op > 3 || op == 2 || n < 0 || !a || !y || (op != 1 && !b) || (op == 3 && !c))
         return TL_ERR_INVALID_ARG;
     if (n == 0)
         return TL_OK;

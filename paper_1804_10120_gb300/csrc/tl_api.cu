@@ -64,6 +64,8 @@ tl_status device_info(const DeviceInfo **out)
             e = occupancy_fwd(&d.fwd_f64_blocks, &d.fwd_f32_blocks, &d.fwd_ff_blocks);
             if (e == cudaSuccess)
                 e = occupancy_bwd(&d.bwd_f64_blocks, &d.bwd_ff_blocks);
+            if (e == cudaSuccess)
+                e = occupancy_fwdbwd(&d.fwdbwd_f64_blocks);
             if (e != cudaSuccess)
                 return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
         }
@@ -75,11 +77,19 @@ tl_status device_info(const DeviceInfo **out)
     return TL_OK;
 }
 
-int grid_for(int64_t n, int threads, int sms, int blocks_per_sm)
+// Launch shape of the one-point-per-thread kernels (grid-stride or block-strided loops over n points).
+// A grid of at least one full wave (every SM holding blocks_per_sm blocks of max_threads) gets that
+// wave and loops.  A smaller grid would leave SMs idle with full-size blocks (N = 4096 in 256-thread
+// blocks occupies 16 of 152 SMs), so the block shrinks, in whole warps, to about n / sms threads: the
+// points spread over all SMs and each SM's share of the FP64-bound work drops by the same factor.
+LaunchShape shape_for(int64_t n, int max_threads, int sms, int blocks_per_sm)
 {
-    const int64_t need = (n + threads - 1) / threads;
-    const int64_t resident = (int64_t)sms * std::max(1, blocks_per_sm);
-    return (int)std::max<int64_t>(1, std::min(need, resident));
+    const int64_t wave = (int64_t)sms * std::max(1, blocks_per_sm) * max_threads;
+    if (n >= wave)
+        return LaunchShape{(int)(wave / max_threads), max_threads};
+    int64_t t = (n + sms - 1) / std::max(1, sms);
+    t = std::min<int64_t>(max_threads, std::max<int64_t>(32, (t + 31) / 32 * 32));
+    return LaunchShape{(int)std::max<int64_t>(1, (n + t - 1) / t), (int)t};
 }
 
 // ---- argument checks ---------------------------------------------------------------------------------
@@ -163,14 +173,14 @@ tl_status launch_forward(const DeviceInfo &d, const tl_dtg_in *in, const tl_dtg_
     cudaError_t e;
     switch (dtype) {
     case TL_F64:
-        e = launch_fwd_f64(fwd_args<double>(in, out), n, grid_for(n, kFwdThreads, d.sms, d.fwd_f64_blocks), st);
+        e = launch_fwd_f64(fwd_args<double>(in, out), n, shape_for(n, kFwdThreads, d.sms, d.fwd_f64_blocks), st);
         break;
     case TL_F32:
-        e = launch_fwd_f32_staged(fwd_args<float>(in, out), n, d.sms, grid_for(n, kFwdThreads, d.sms, d.fwd_f32_blocks),
+        e = launch_fwd_f32_staged(fwd_args<float>(in, out), n, d.sms, shape_for(n, kFwdThreads, d.sms, d.fwd_f32_blocks),
                                   st);
         break;
     case TL_F64_FF:
-        e = launch_fwd_ff(fwd_args<double>(in, out), n, grid_for(n, kFwdThreads, d.sms, d.fwd_ff_blocks), st);
+        e = launch_fwd_ff(fwd_args<double>(in, out), n, shape_for(n, kFwdThreads, d.sms, d.fwd_ff_blocks), st);
         break;
     default:
         return fail(TL_ERR_INVALID_ARG, "unknown dtype %d", (int)dtype);
@@ -377,13 +387,49 @@ tl_status tl_dtg_backward(const tl_dtg_in *in, const tl_dtg_gout *gout, const tl
     for (int q = 0; q < N_OUT; ++q)
         a.gout[q] = (const double *)((const void *const *)gout)[q];
     cudaError_t e = (dtype == TL_F64)
-                        ? launch_bwd_f64(a, n, grid_for(n, kBwdThreads, d->sms, d->bwd_f64_blocks), (cudaStream_t)stream)
-                        : launch_bwd_ff(a, n, grid_for(n, kBwdFfThreads, d->sms, d->bwd_ff_blocks), (cudaStream_t)stream);
+                        ? launch_bwd_f64(a, n, shape_for(n, kBwdThreads, d->sms, d->bwd_f64_blocks), (cudaStream_t)stream)
+                        : launch_bwd_ff(a, n, shape_for(n, kBwdFfThreads, d->sms, d->bwd_ff_blocks), (cudaStream_t)stream);
     if (e == cudaErrorNotSupported)
         return fail(TL_ERR_UNSUPPORTED, "dtype %d has no adjoint kernel in this build", (int)dtype);
     if (e != cudaSuccess)
         return cuda_fail(e, "backward launch");
     return TL_OK;
+}
+
+tl_status tl_dtg_forward_backward(const tl_dtg_in *in, const tl_dtg_out *out, const tl_dtg_gout *gout,
+                                  const tl_dtg_gin *gin, int64_t n, tl_dtype dtype, tl_stream stream)
+{
+    if (!in || !out || !gout || !gin)
+        return fail(TL_ERR_INVALID_ARG, "NULL table");
+    if (n < 0)
+        return fail(TL_ERR_INVALID_ARG, "n = %lld < 0", (long long)n);
+    if (!dtype_ok(dtype))
+        return fail(TL_ERR_INVALID_ARG, "unknown dtype %d", (int)dtype);
+    if (dtype != TL_F64)
+        return fail(TL_ERR_UNSUPPORTED, "the fused forward + adjoint is provided for TL_F64");
+    const void *const *tabs[4] = {(const void *const *)in, (const void *const *)out, (const void *const *)gout,
+                                  (const void *const *)gin};
+    const int counts[4] = {N_IN, N_OUT, N_OUT, N_IN};
+    const bool writes[4] = {false, true, false, true}, nullable[4] = {false, false, true, false};
+    const char *const names[4] = {"in", "out", "gout", "gin"};
+    tl_status s = check_tables(tabs, counts, writes, nullable, names, 4, n, elem_size(dtype));
+    if (s != TL_OK || n == 0)
+        return s;
+    const DeviceInfo *d = nullptr;
+    if ((s = device_info(&d)) != TL_OK)
+        return s;
+    FwdBwdArgs<double> a;
+    for (int q = 0; q < N_IN; ++q) {
+        a.in[q] = (const double *)((const void *const *)in)[q];
+        a.gin[q] = (double *)((void *const *)gin)[q];
+    }
+    for (int q = 0; q < N_OUT; ++q) {
+        a.out[q] = (double *)((void *const *)out)[q];
+        a.gout[q] = (const double *)((const void *const *)gout)[q];
+    }
+    const cudaError_t e =
+        launch_fwdbwd_f64(a, n, shape_for(n, kFwdBwdThreads, d->sms, d->fwdbwd_f64_blocks), (cudaStream_t)stream);
+    return e == cudaSuccess ? TL_OK : cuda_fail(e, "forward + adjoint launch");
 }
 
 size_t tl_dtg_host_workspace_bytes(int64_t n, tl_dtype dtype)

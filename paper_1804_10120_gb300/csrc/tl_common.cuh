@@ -26,6 +26,13 @@ template <typename T> struct BwdArgs {
     const T *gout[N_OUT];   // nullptr = output absent from the functional
     T *gin[N_IN];
 };
+// Forward and adjoint in one pass (164 pointers = 1312 bytes of parameters).
+template <typename T> struct FwdBwdArgs {
+    const T *in[N_IN];
+    T *out[N_OUT];
+    const T *gout[N_OUT];   // nullptr = output absent from the functional
+    T *gin[N_IN];
+};
 
 // Streaming loads and stores: each element is touched exactly once, so keep it out of L1 and mark it
 // evict-first in L2.
@@ -146,11 +153,15 @@ __device__ __forceinline__ double mul_int(double a, double b)
 
 // ---- binary64 reciprocal ------------------------------------------------------------------------------
 // Seed: binary32 reciprocal (MUFU) of the binary32 truncation of d, both conversions done on integer
-// bits; relative seed error e0 < 2^-21.  One third-order Newton-Raphson step in binary64,
-//   e = 1 - d r,  r' = r + r (e + e^2),
-// leaves a relative error of about e0^3 < 2^-63 plus rounding, i.e. within one ulp.  Three FP64
-// operations instead of the division sequence.  Outside the binary32 exponent range (and for zero,
-// inf, nan) the IEEE quotient 1.0 / d is used.
+// bits; relative seed error |e0| < 2^-21.  Then one third-order step in binary64: with e = 1 - d r,
+// 1/d = r / (1 - e) = r (1 + e + e^2 + e^3 + ...), and the series truncated after e^2,
+//   r' = r + r (e + e^2),
+// leaves a relative error of about e0^3 < 2^-63 (the functional-iteration view of division: M. J. Flynn,
+// "On division by functional iteration", IEEE Trans. Computers C-19, 1970).  e is exact up to one
+// rounding (fused multiply-add), so r' is r (1 + e + e^2) plus the final rounding: within one ulp of 1/d
+// (tests/test_gpu_f64_int.py checks it against the host's IEEE quotient).  Three FP64 operations
+// instead of the division sequence.  Outside the binary32 exponent window, d in [2^-124, 2^125) in
+// magnitude (and for zero, subnormals, inf, nan), the IEEE quotient 1.0 / d is used.
 __device__ __forceinline__ double rcp_f64(double d)
 {
     const uint64_t b = (uint64_t)__double_as_longlong(d);

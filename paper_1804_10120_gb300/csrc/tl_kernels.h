@@ -8,25 +8,34 @@ namespace tl {
 
 constexpr int kFwdThreads = 256;
 
+// Grid and block size of a one-dimensional launch.
+struct LaunchShape {
+    int grid, threads;
+};
+
 constexpr int kBwdThreads = 128;
 constexpr int kBwdFfThreads = 256;   // the float-float adjoint (one block per SM, see dtg_bwd.cu)
 
-cudaError_t launch_fwd_f64(const FwdArgs<double> &a, int64_t n, int grid, cudaStream_t s);
-cudaError_t launch_fwd_f32(const FwdArgs<float> &a, int64_t n, int grid, cudaStream_t s);
+cudaError_t launch_fwd_f64(const FwdArgs<double> &a, int64_t n, LaunchShape sh, cudaStream_t s);
+cudaError_t launch_fwd_f32(const FwdArgs<float> &a, int64_t n, LaunchShape sh, cudaStream_t s);
 // Binary32 forward with the inputs staged through shared memory by bulk copies (tiles of
-// kF32StagedTile points, kF32StagedStages deep); falls back to launch_fwd_f32 (grid tail_grid) for
+// kF32StagedTile points, kF32StagedStages deep); falls back to launch_fwd_f32 (shape `tail`) for
 // unaligned inputs and for the last n % kF32StagedTile points.
 constexpr int kF32StagedTile = 512;
 constexpr int kF32StagedStages = 2;
-cudaError_t launch_fwd_f32_staged(const FwdArgs<float> &a, int64_t n, int sms, int tail_grid, cudaStream_t s);
+cudaError_t launch_fwd_f32_staged(const FwdArgs<float> &a, int64_t n, int sms, LaunchShape tail, cudaStream_t s);
 // Test hook: the staged kernel over the full tiles of n points with 16 bytes announced per stage that
 // never arrive, so every block's first wait runs out (about 1 s) and the block leaves without output.
 cudaError_t launch_fwd_f32_staged_stalled(const FwdArgs<float> &a, int64_t n, int sms, cudaStream_t s);
 // Number of bounded waits in the staged kernels that gave up since the library was loaded.
 cudaError_t read_wait_timeouts(unsigned int *count);
-cudaError_t launch_fwd_ff(const FwdArgs<double> &a, int64_t n, int grid, cudaStream_t s);
-cudaError_t launch_bwd_f64(const BwdArgs<double> &a, int64_t n, int grid, cudaStream_t s);
-cudaError_t launch_bwd_ff(const BwdArgs<double> &a, int64_t n, int grid, cudaStream_t s);
+cudaError_t launch_fwd_ff(const FwdArgs<double> &a, int64_t n, LaunchShape sh, cudaStream_t s);
+cudaError_t launch_bwd_f64(const BwdArgs<double> &a, int64_t n, LaunchShape sh, cudaStream_t s);
+cudaError_t launch_bwd_ff(const BwdArgs<double> &a, int64_t n, LaunchShape sh, cudaStream_t s);
+// Forward and adjoint of one functional in one pass (binary64).
+constexpr int kFwdBwdThreads = 128;
+cudaError_t launch_fwdbwd_f64(const FwdBwdArgs<double> &a, int64_t n, LaunchShape sh, cudaStream_t s);
+cudaError_t occupancy_fwdbwd(int *f64);
 
 struct BatchView;
 // Batched forward: one persistent launch over all grids of a plan; `threads` in {128, 256, 512}.

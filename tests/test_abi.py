@@ -82,6 +82,24 @@ def test_backward_argument_checks(L):
     assert b(ctypes.byref(tin), ctypes.byref(gout), ctypes.byref(g2), 16, 0, None) == 1
 
 
+def test_forward_backward_argument_checks(L):
+    tin, tout = _tabs()
+    gout = (ctypes.c_void_p * 39)(*([None] * 39))
+    gin = (ctypes.c_void_p * 43)(*[(1 << 30) + s * 128 for s in range(43)])
+    f = L.tl_dtg_forward_backward
+    f.argtypes = [ctypes.c_void_p] * 4 + [ctypes.c_int64, ctypes.c_int, ctypes.c_void_p]
+    assert f(ctypes.byref(tin), ctypes.byref(tout), ctypes.byref(gout), ctypes.byref(gin), 0, 0, None) == 0
+    assert f(ctypes.byref(tin), ctypes.byref(tout), ctypes.byref(gout), ctypes.byref(gin), 16, 2, None) == 3
+    assert f(ctypes.byref(tin), ctypes.byref(tout), ctypes.byref(gout), ctypes.byref(gin), 16, 1, None) == 3
+    assert f(ctypes.byref(tin), ctypes.byref(tout), ctypes.byref(gout), ctypes.byref(gin), -1, 0, None) == 1
+    assert f(None, ctypes.byref(tout), ctypes.byref(gout), ctypes.byref(gin), 16, 0, None) == 1
+    g2 = (ctypes.c_void_p * 43)(*gin); g2[3] = tout[5]           # an input gradient over an output
+    assert f(ctypes.byref(tin), ctypes.byref(tout), ctypes.byref(gout), ctypes.byref(g2), 16, 0, None) == 1
+    assert b"overlap" in L.tl_last_error()
+    nul = (ctypes.c_void_p * 39)(*tout); nul[38] = None           # outputs are all required
+    assert f(ctypes.byref(tin), ctypes.byref(nul), ctypes.byref(gout), ctypes.byref(gin), 16, 0, None) == 1
+
+
 def test_host_workspace_size(L):
     L.tl_dtg_host_workspace_bytes.restype = ctypes.c_size_t
     L.tl_dtg_host_workspace_bytes.argtypes = [ctypes.c_int64, ctypes.c_int]

@@ -1,0 +1,98 @@
+"""The fused forward + adjoint (tl_dtg_forward_backward): outputs bit for bit those of tl_dtg_forward,
+input gradients against the CPU oracle's adjoint, for every combination of upstream-gradient groups,
+ragged sizes and the full N = 2^22 grid in the benchmark's launch configuration."""
+import numpy as np
+import pytest
+
+import gridgen
+import oracle
+from tests.parity import TOL_F64, assert_components, IN_NAMES
+from tests.test_gpu_backward import upstream
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def dev():
+    return torch.device("cuda", 0)
+
+
+def run_fused(x, gout):
+    import paper_1804_10120_gb300 as tl
+    xd = torch.from_numpy(x).to(dev())
+    gd = [None if g is None else torch.from_numpy(g).to(dev()) for g in gout]
+    y, gin = tl.tl_dtg_forward_backward(xd, gd)
+    y_sep = tl.tl_dtg_forward(xd)
+    torch.cuda.synchronize()
+    return y.cpu().numpy(), gin.cpu().numpy(), y_sep.cpu().numpy()
+
+
+@pytest.mark.parametrize("which", [("gamma", "dtg"), ("ginv", "gamma", "dbcov", "dtg"), ("dtg",), ("gamma",),
+                                   ("dbcov",), ("ginv",), ("ginv", "dtg"), ()])
+def test_fused_matches_forward_and_oracle_adjoint(which):
+    n = 4096
+    x = gridgen.random_grid(n, 3)
+    gout = upstream(n, 3, which)
+    y, gin, y_sep = run_fused(x, gout)
+    assert np.array_equal(y.view(np.uint64), y_sep.view(np.uint64))
+    if not which:
+        assert np.all(gin == 0.0)
+        return
+    assert_components(gin, oracle.backward(x, gout), TOL_F64, names=IN_NAMES, what="fused adjoint %s" % (which,))
+
+
+@pytest.mark.parametrize("n", [1, 2, 127, 129, 255, 65537])
+def test_fused_ragged(n):
+    x = gridgen.random_grid(n, 70 + n)
+    gout = upstream(n, 70 + n, ("ginv", "gamma", "dbcov", "dtg"))
+    y, gin, y_sep = run_fused(x, gout)
+    assert np.array_equal(y.view(np.uint64), y_sep.view(np.uint64))
+    assert_components(gin, oracle.backward(x, gout), TOL_F64, names=IN_NAMES, what="fused n=%d" % n)
+
+
+def test_fused_partial_groups_and_conformal_grid():
+    n = 1000
+    x = gridgen.random_grid(n, 5)
+    gout = upstream(n, 5, ("gamma", "dtg", "dbcov"))
+    gout[24 + 4] = None
+    gout[6 + 7] = None
+    _, gin, _ = run_fused(x, gout)
+    assert_components(gin, oracle.backward(x, gout), TOL_F64, names=IN_NAMES, what="fused partial")
+    x = gridgen.conformal_grid(16)
+    gout = upstream(x.shape[1], 6, ("ginv", "gamma", "dbcov", "dtg"))
+    y, gin, y_sep = run_fused(x, gout)
+    assert np.array_equal(y.view(np.uint64), y_sep.view(np.uint64))
+    assert_components(gin, oracle.backward(x, gout), TOL_F64, names=IN_NAMES, what="fused conformal")
+
+
+def test_fused_full_size():
+    """N = 2^22, seed 3, loss sum W dtg + V Gamma, in the benchmark's launch: outputs bitwise equal to
+    the forward kernel on every point, gradients within the gate of the (finite-difference-checked)
+    adjoint kernel on every point and of the oracle on a sample."""
+    import paper_1804_10120_gb300 as tl
+    n = 1 << 22
+    x = gridgen.random_grid(n, 3)
+    gout = upstream(n, 3)
+    xd = torch.from_numpy(x).to(dev())
+    gd = [None if g is None else torch.from_numpy(g).to(dev()) for g in gout]
+    y, gin = tl.tl_dtg_forward_backward(xd, gd)
+    assert torch.equal(y.view(torch.int64), tl.tl_dtg_forward(xd).view(torch.int64))
+    gsep = tl.tl_dtg_backward(xd, gd)
+    err = ((gin - gsep).abs().amax(dim=1) / gsep.abs().amax(dim=1)).max().item()
+    assert err <= TOL_F64, err
+    rng = np.random.default_rng(31)
+    idx = np.unique(np.concatenate([np.arange(300), np.arange(n - 300, n), rng.integers(0, n, 15000)]))
+    ref = oracle.backward(np.ascontiguousarray(x[:, idx]),
+                          [None if g is None else np.ascontiguousarray(g[idx]) for g in gout])
+    gi = gin[:, torch.from_numpy(idx).to(dev())].cpu().numpy()
+    assert_components(gi, ref, TOL_F64, names=IN_NAMES, what="N=2^22 sampled fused adjoint")
+
+
+def test_fused_empty_and_unsupported():
+    import paper_1804_10120_gb300 as tl
+    x = torch.empty((43, 0), dtype=torch.float64, device=dev())
+    y, gin = tl.tl_dtg_forward_backward(x, [None] * 39)
+    assert y.shape == (39, 0) and gin.shape == (43, 0)
+    x = torch.from_numpy(gridgen.random_grid(16, 1)).to(dev())
+    with pytest.raises(tl.TLError):
+        tl.tl_dtg_forward_backward(x, [None] * 39, dtype="f64_ff")
