@@ -176,10 +176,14 @@ TL_API void tl_batch_plan_destroy(tl_batch_plan *plan);
  * Nothing is allocated by the library -- no cudaMalloc / cudaFree, no allocating library routine.
  * The first call on a device performs a one-time set-up on that device (it resolves the array's
  * device address), so make that first call before any stream capture.  Each call copies the tables
- * from host memory into the array on `stream` (these copies come from pageable memory and synchronise
- * with the host), then launches.  Every call shares the one array and leaves its contents behind:
- * calls whose work overlaps on the GPU (different streams, or host threads racing) corrupt each
- * other's tables -- order them on one stream.  Error behaviour as for the other entry points.
+ * from a static host image into the array on `stream` (these copies come from pageable memory and
+ * synchronise with the host), then launches.  Because the next call reuses that host image, a call
+ * made while `stream` is being captured returns TL_ERR_UNSUPPORTED and enqueues nothing.  Every call
+ * shares the one array and leaves its contents behind: calls whose work overlaps on the GPU
+ * (different streams, or host threads racing) corrupt each other's tables -- order them on one
+ * stream.  The tables are built by the call itself from the validated arguments, so there is no
+ * plan-consistency status to report (no counterpart of tl_batch_plan_check).  Error behaviour as for
+ * the other entry points.
  */
 TL_API tl_status tl_dtg_batched_noalloc(const tl_dtg_in *in, const tl_dtg_out *out, const int64_t *n, int32_t G,
                                         tl_dtype dtype, tl_stream stream);

@@ -58,13 +58,21 @@ extern "C" TL_API tl_status tl_dtg_batched_noalloc(const tl_dtg_in *in, const tl
                     kNoAllocMaxGrids);
     if (!dtype_ok(dtype))
         return fail(TL_ERR_INVALID_ARG, "unknown dtype %d", (int)dtype);
+    // The tables travel through a static host image that the next call overwrites, so a copy recorded
+    // into a graph would replay the wrong grids' tables: refuse during stream capture, before anything
+    // (including the one-time set-up) touches the stream or the device.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing((cudaStream_t)stream, &cap);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "cudaStreamIsCapturing");
+    if (cap != cudaStreamCaptureStatusNone)
+        return fail(TL_ERR_UNSUPPORTED, "tl_dtg_batched_noalloc cannot be called while its stream is being captured");
     const DeviceInfo *di = nullptr;
     tl_status s = device_info(&di);
     if (s != TL_OK)
         return s;
     int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess)
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess)
         return cuda_fail(e, "cudaGetDevice");
 
     std::lock_guard<std::mutex> lk(g_na_mu);
