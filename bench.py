@@ -8,8 +8,10 @@ achieved HBM GB/s counts the paper's effective bandwidth, 8 bytes x (43 + 39) co
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--variant f64|f64_ff|f32]
 
-Under torchrun every rank runs its own grid (the points are independent; no collective on the data
-path): weak scaling, value = all ranks' points / max over ranks of the timed region.
+With N > 1 every rank runs its own grid on its own GPU (the points are independent; no collective on
+the data path): weak scaling, value = all ranks' points / max over ranks of the timed region.  Under
+torchrun the ranks come from WORLD_SIZE / RANK / LOCAL_RANK, which must agree with --gpus; without a
+launcher, --gpus N > 1 re-runs this script under torch.distributed.run with N ranks.
 """
 import argparse
 import hashlib
@@ -42,11 +44,15 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the measurements of the other forms")
-    ap.add_argument("--only", default=None, choices=["forward", "adjoint", "batched", "fd", "generated"],
+    ap.add_argument("--only", default=None, choices=["forward", "adjoint", "fwdbwd", "batched", "fd", "generated"],
                     help="run just one form on --n points (or --grids subgrids) and print its timing; for profiling")
     ap.add_argument("--grids", type=int, default=600)
     ap.add_argument("--order", type=int, default=4, choices=[2, 4], help="difference order of --only fd")
     ap.add_argument("--suite", default=None, help="comma-separated grid sizes: run the Eqs. 9-21 expression suite")
+    ap.add_argument("--probe", action="store_true",
+                    help="issue rates of the FP64 pipe (DFMA, DADD, DMUL, F2F pairs) per SM and clock, one JSON line")
+    ap.add_argument("--launcher-check", action="store_true",
+                    help="no GPU work: each rank builds its grid and reports it; rank 0 prints the ranks' view")
     return ap.parse_args()
 
 
@@ -163,6 +169,67 @@ def dist_setup():
     return world, rank, local
 
 
+def _free_port():
+    import socket
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def replica_command(gpus, argv, port):
+    """The command that runs this script as `gpus` ranks on one node (one rank per GPU)."""
+    return [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", str(gpus),
+            "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.abspath(__file__)] + list(argv)
+
+
+def check_ranks(args):
+    """Returns None when the rank layout matches --gpus, else an exit code after re-running under a
+    launcher (no WORLD_SIZE and --gpus > 1) or refusing a layout that contradicts --gpus."""
+    if "WORLD_SIZE" not in os.environ:
+        if args.gpus > 1:
+            return subprocess.call(replica_command(args.gpus, sys.argv[1:], _free_port()))
+        return None
+    world = int(os.environ["WORLD_SIZE"])
+    if world != args.gpus:
+        print("bench.py: WORLD_SIZE=%d but --gpus %d" % (world, args.gpus), file=sys.stderr)
+        return 2
+    return None
+
+
+def launcher_check(args):
+    """The replica layout without GPU work: every rank builds its own grid (gloo process group when
+    there are several ranks), the ranks agree on the slowest rank's time, and rank 0 prints what each
+    rank held.  Exercises the launcher, the per-rank seeds and the max over ranks on any machine."""
+    import gridgen
+    world, rank, _ = dist_setup()
+    t0 = time.perf_counter()
+    x = gridgen.random_grid(4096, rank_seed(rank))
+    digest = hashlib.sha256(x.tobytes()).hexdigest()[:16]
+    local_ms = (time.perf_counter() - t0) * 1e3
+    views = [(rank, rank_seed(rank), digest)]
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+
+        def max_over(v):
+            t = torch.tensor([v], dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            return float(t.item())
+        t_max, _ = replica_throughput(local_ms, 4096, 1, world, max_over)
+        gathered = [None] * world
+        dist.all_gather_object(gathered, views[0])
+        views = gathered
+        dist.destroy_process_group()
+    else:
+        t_max = local_ms
+    if rank == 0:
+        print(json.dumps({"launcher_check": True, "n_gpus": world, "gpus_arg": args.gpus, "t_max_ms": t_max,
+                          "ranks": [{"rank": r, "seed": s, "grid_sha": d} for r, s, d in views]}), flush=True)
+
+
 def cpu_threads():
     try:
         return len(os.sched_getaffinity(0))
@@ -252,13 +319,85 @@ def reference_arm(args):
 #   18, Eq. 6 contraction 90, covariant shift derivative 39 (the 6 distinct sums Gamma^k_ij beta_k and 9
 #   subtractions), Eq. 5 15.
 FLOPS_F64_PER_POINT = 197
-# The FP64 pipe issues 2 operations (DFMA, DADD or DMUL alike) per clock per SM:
-FP64_OPS_PER_S = 2 * 152 * 2.07e9                # x 152 SMs x 2070 MHz
 # Of the 197 flops, the 37 products that are not fused into an FMA run on the integer pipes (mul_int,
 # bit-identical to the FP64 multiply), and the FP64 pipe executes 71 DFMA + 18 DADD = 89 operations per
-# point.  The arithmetic roof of this instruction mix is reached when those 89 operations fill the pipe:
+# point.  The pipe issues DFMA and DADD at the same rate (tl_testing_pipe_rate), so the kernel's second
+# ceiling is that rate / 89 points per second.
 FP64_OPS_PER_POINT = 89
-ALU_TFLOPS_PEAK = FP64_OPS_PER_S * FLOPS_F64_PER_POINT / FP64_OPS_PER_POINT / 1e12
+# The fused forward + adjoint for the loss sum W d_t g + V Gamma: 1192 bytes per point (43 inputs and
+# 24 upstream gradients read, 39 outputs and 43 input gradients written) and 223 FP64-pipe operations
+# (the forward's 89; Kbar/alphabar 5, betabar 15, Gammabar 18, Tbar 36, the bracket scatter 12 and the
+# folded -H A H as 2 Tbar Gamma^T 48).  The adjoint alone: 808 bytes and 181 operations; the forward
+# and the adjoint launched one after the other: 1464 bytes and 270 operations.
+FWDBWD_BYTES_PER_POINT, FWDBWD_FP64_OPS = 1192, 223
+BWD_BYTES_PER_POINT, BWD_FP64_OPS = 808, 181
+
+
+def device_facts(dev):
+    """SM count from the device, maximum SM clock from nvidia-smi (MHz; None if unavailable)."""
+    import torch
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = None
+    try:
+        out = subprocess.run(["nvidia-smi", "-i", str(dev.index), "--query-gpu=clocks.max.sm",
+                              "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=20)
+        mhz = float(out.stdout.strip().splitlines()[0])
+    except Exception:
+        pass
+    return sms, mhz
+
+
+PROBE_OPS = {0: "DFMA", 1: "DADD", 2: "DMUL", 3: "F2F pair (binary64->binary32->binary64)",
+             4: "addition as DFMA by 1.0"}
+
+
+def pipe_rates(dev, stream, ops=(0, 1, 2, 3, 4), target_ms=40.0):
+    """Issue rate of each probed operation, operations (op 3: conversion pairs) per second over the whole
+    GPU: 8 blocks of 256 threads per SM, 8 independent chains per thread, timed with CUDA events on
+    `stream` (the kernel: tl_testing_pipe_rate)."""
+    import ctypes
+    import torch
+    import paper_1804_10120_gb300 as tl
+    L = tl.lib()
+    L.tl_testing_pipe_rate.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                       ctypes.c_void_p, ctypes.c_void_p]
+    L.tl_testing_pipe_rate.restype = ctypes.c_int
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    blocks, threads = 8 * sms, 256
+    sink = torch.empty(blocks * threads, dtype=torch.float64, device=dev)
+    h = ctypes.c_void_p(stream.cuda_stream)
+    rates = {}
+    for op in ops:
+        iters = 256
+        while True:
+            def run(it=iters):
+                assert L.tl_testing_pipe_rate(op, it, blocks, threads, ctypes.c_void_p(sink.data_ptr()), h) == 0
+            ms = cuda_time(run, 3, stream, warmup=1)
+            if ms >= target_ms or iters >= (1 << 24):
+                break
+            iters *= 2 if ms < target_ms / 4 else 1 + int(target_ms / max(ms, 1e-3))
+        rates[op] = blocks * threads * 8 * iters / (ms * 1e-3)
+    return rates
+
+
+def probe_main(args):
+    """--probe: the FP64 pipe's issue rates on this GPU, per SM per clock at the clocks sampled meanwhile."""
+    import torch
+    from paper_1804_10120_gb300 import build as tlbuild
+    tlbuild.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    sms, max_mhz = device_facts(dev)
+    pipe_rates(dev, stream, ops=(0,), target_ms=10.0)      # warm up clocks and module
+    with ClockSampler(dev.index) as clk:
+        rates = pipe_rates(dev, stream)
+    c = clk.summary()
+    mhz = c.get("sm_mhz") or max_mhz
+    print(json.dumps({"probe": "FP64 pipe issue rates", "sms": sms, "sm_max_mhz": max_mhz, "clocks": c,
+                      "ops": {PROBE_OPS[k]: {"per_s": v, "per_clk_per_sm_at_sampled_clock": v / (sms * mhz * 1e6),
+                                             "per_clk_per_sm_at_max_clock": v / (sms * max_mhz * 1e6) if max_mhz else None}
+                              for k, v in rates.items()}}), flush=True)
 
 
 def _max_over_ranks(v, dev):
@@ -334,7 +473,7 @@ def small_grid(dev, stream):
                       "the launching stream before each launch"}
 
 
-def extras(dev, stream, steps, x64, hbm):
+def extras(dev, stream, steps, x64, hbm, fp64_rate=None):
     """The other forms of the path, each against the plain binary64 single-grid kernel, same GPU."""
     import torch
     import gridgen
@@ -369,16 +508,28 @@ def extras(dev, stream, steps, x64, hbm):
     ms_fb_ff = cuda_time(lambda: (tl.tl_dtg_forward(x3, y3, dtype="f64_ff", stream=stream),
                                   tl.tl_dtg_backward(x3, gout, g3, dtype="f64_ff", stream=stream)), steps, stream)
     ms_b_ff = cuda_time(lambda: tl.tl_dtg_backward(x3, gout, g3, dtype="f64_ff", stream=stream), steps, stream)
+    ms_fused = cuda_time(lambda: tl.tl_dtg_forward_backward(x3, gout, y3, g3, stream=stream), steps, stream)
     out["fwd_adjoint_ff"] = {"workload": "N=2^22, seed 3, L = sum W dtg + V Gamma", "ms_adjoint": ms_b_ff,
                              "ms": ms_fb_ff, "points_per_s": n3 / ms_fb_ff * 1e3, "GB_s": 1464 * n3 / ms_fb_ff / 1e6,
                              "hbm_frac": 1464 * n3 / ms_fb_ff / 1e6 / hbm,
                              "arith": "float-float forward and adjoint (binary64 inverse, bracket, folds)"}
-    out["fwd_adjoint"] = {"workload": "N=2^22, seed 3, L = sum W dtg + V Gamma", "ms_forward": ms_f,
-                          "ms_adjoint": ms_b, "ms": ms_fb, "points_per_s": n3 / ms_fb * 1e3,
-                          "GB_s": 1464 * n3 / ms_fb / 1e6, "hbm_frac": 1464 * n3 / ms_fb / 1e6 / hbm,
-                          "adjoint_GB_s": 808 * n3 / ms_b / 1e6,
-                          "bytes_per_point": "forward 656 + adjoint 808 (34 inputs: d_j beta_i is not needed, "
-                                             "24 upstream gradients, 43 input gradients)"}
+    out["fwd_adjoint"] = {
+        "workload": "N=2^22, seed 3, L = sum W dtg + V Gamma (W, V ~ N(0,1)), binary64",
+        "fused": {"entry_point": "tl_dtg_forward_backward", "ms": ms_fused, "points_per_s": n3 / ms_fused * 1e3,
+                  "bytes_per_point": FWDBWD_BYTES_PER_POINT,
+                  "GB_s": FWDBWD_BYTES_PER_POINT * n3 / ms_fused / 1e6,
+                  "hbm_frac": FWDBWD_BYTES_PER_POINT * n3 / ms_fused / 1e6 / hbm,
+                  "fp64_ops_per_point": FWDBWD_FP64_OPS,
+                  "fp64_frac": FWDBWD_FP64_OPS * n3 / (ms_fused * 1e-3) / fp64_rate if fp64_rate else None},
+        "separate": {"ms_forward": ms_f, "ms_adjoint": ms_b, "ms": ms_fb, "points_per_s": n3 / ms_fb * 1e3,
+                     "bytes_per_point": 656 + BWD_BYTES_PER_POINT, "GB_s": 1464 * n3 / ms_fb / 1e6,
+                     "hbm_frac": 1464 * n3 / ms_fb / 1e6 / hbm,
+                     "adjoint_hbm_frac": BWD_BYTES_PER_POINT * n3 / ms_b / 1e6 / hbm,
+                     "adjoint_fp64_frac": BWD_FP64_OPS * n3 / (ms_b * 1e-3) / fp64_rate if fp64_rate else None},
+        "bytes_per_point": "fused 1192 (43 inputs + 24 upstream gradients read, 39 outputs + 43 input gradients "
+                           "written); adjoint alone 808 (34 inputs: d_j beta_i is not needed, 24 upstream "
+                           "gradients, 43 input gradients)",
+        "fp64_rate_source": "DFMA issue rate of tl_testing_pipe_rate, same run"}
     del x3, W, V, gout, y3, g3
     # batched: 600 subgrids n^3, n ~ U{8..48} (seed 2)
     sides = gridgen.subgrid_sides(600, 2)
@@ -497,6 +648,15 @@ def only_form(args):
         adj_dtype = "f64_ff" if args.variant == "f64_ff" else "f64"
         fn = lambda: tl.tl_dtg_backward(x, gout, g, dtype=adj_dtype, stream=stream)
         units = n
+    elif args.only == "fwdbwd":
+        x = torch.from_numpy(gridgen.random_grid(n, 3)).to(dev)
+        W = torch.from_numpy(gridgen.normal_fields(6, n, 3, 1000)).to(dev)
+        V = torch.from_numpy(gridgen.normal_fields(18, n, 3, 1100)).to(dev)
+        gout = [None] * 6 + [V[i] for i in range(18)] + [None] * 9 + [W[i] for i in range(6)]
+        y = torch.empty((39, n), dtype=torch.float64, device=dev)
+        g = torch.empty((43, n), dtype=torch.float64, device=dev)
+        fn = lambda: tl.tl_dtg_forward_backward(x, gout, y, g, stream=stream)
+        units = n
     elif args.only == "fd":
         side = round(n ** (1.0 / 3.0))
         shape = (side, side, side)
@@ -579,6 +739,13 @@ def suite(dev, stream, sizes, reps=10):
 
 def main():
     args = parse()
+    rc = check_ranks(args)
+    if rc is not None:
+        sys.exit(rc)
+    if args.launcher_check:
+        return launcher_check(args)
+    if args.probe:
+        return probe_main(args)
     if args.suite:
         import torch
         from paper_1804_10120_gb300 import build as tlbuild
@@ -646,26 +813,23 @@ def main():
     bpp = BYTES_PER_POINT[variant]
     gbs = bpp * n / avg_launch_s / 1e9
     traffic = traffic_per_launch(KERNEL_NAME[variant], n)
+    roofline = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                "traffic": traffic, "peak_source": peak_kind + " (MEASURED_PEAKS.json copy bandwidth)",
+                "kernel": KERNEL_NAME[variant], "bytes_per_point": bpp, "avg_launch_ms": avg_launch_s * 1e3}
+    sms, max_mhz = device_facts(dev)
+    fp64 = None
     if variant == "f64":
-        # binary64 arithmetic is bound by the FP64 pipe (1/64 of the FP32 rate on this part), not by HBM
-        tf = FLOPS_F64_PER_POINT * n / avg_launch_s / 1e12
-        roofline = {"bound": "alu", "achieved": tf, "peak": ALU_TFLOPS_PEAK, "unit": "TFLOP/s",
-                    "frac": tf / ALU_TFLOPS_PEAK, "traffic": traffic,
-                    "peak_source": "derived: the FP64 pipe issues 2 operations/clk/SM x 152 SMs x 2070 MHz = "
-                                   "629 G operations/s; the chain puts 89 of them per point on it (71 DFMA + "
-                                   "18 DADD; its 37 stand-alone products run on the integer pipes), so its 197 "
-                                   "flops per point cost 89 FP64 issue slots: roof = 629e9 x 197 / 89",
-                    "fp64_pipe": {"ops_per_point": FP64_OPS_PER_POINT,
-                                  "achieved_gops": FP64_OPS_PER_POINT * n / avg_launch_s / 1e9,
-                                  "peak_gops": FP64_OPS_PER_S / 1e9},
-                    "kernel": KERNEL_NAME[variant], "flops_per_point": FLOPS_F64_PER_POINT,
-                    "avg_launch_ms": avg_launch_s * 1e3,
-                    "hbm": {"achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
-                            "bytes_per_point": bpp, "peak_source": peak_kind}}
-    else:
-        roofline = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
-                    "traffic": traffic, "peak_source": peak_kind, "kernel": KERNEL_NAME[variant],
-                    "bytes_per_point": bpp, "avg_launch_ms": avg_launch_s * 1e3}
+        # the second ceiling of the binary64 chain: the FP64 pipe (1/64 of the FP32 rate on this part),
+        # whose DFMA issue rate is measured here by the probe kernel, after the timed region
+        rate = pipe_rates(dev, stream, ops=(0,), target_ms=20.0)[0]
+        ach = FP64_OPS_PER_POINT * n / avg_launch_s
+        fp64 = {"ops_per_point": FP64_OPS_PER_POINT, "achieved_gops": ach / 1e9, "peak_gops": rate / 1e9,
+                "frac": ach / rate, "peak_source": "measured: DFMA issue rate of tl_testing_pipe_rate on this GPU, "
+                                                  "same run (8 x 256-thread blocks per SM, 8 chains per thread)",
+                "nominal_peak_gops": 2 * sms * max_mhz / 1e3 if max_mhz else None,
+                "nominal_source": "2 operations/clk/SM x %d SMs x %s MHz (device, nvidia-smi)" % (sms, max_mhz),
+                "floor_ms": FP64_OPS_PER_POINT * n / rate * 1e3}
+        roofline["second_ceiling"] = {"unit": "FP64 pipe operations/s", **fp64}
 
     # end to end through the host-buffer C entry point: H2D of the inputs and D2H of the outputs inside
     # the timed region, page-locked host memory
@@ -696,7 +860,8 @@ def main():
 
     forms = None
     if rank == 0 and world == 1 and not args.no_extras and variant != "f32" and n == N_FULL:
-        forms = extras(dev, stream, max(5, min(args.steps, 20)), x, hbm)
+        forms = extras(dev, stream, max(5, min(args.steps, 20)), x, hbm,
+                       fp64["peak_gops"] * 1e9 if fp64 else None)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:

@@ -31,13 +31,27 @@ TL_API tl_status tl_testing_ff(int op, const double *a, const double *b, const d
  * tl_testing_f64_int applies one binary64 operation elementwise, as the kernels' integer-pipe form or
  * the hardware instruction, so the integer forms can be checked bit for bit:
  *   op 0: y[i] = a[i] * b[i]           (integer-pipe product, mul_int)
+ *   op 1: y[i] = 1 / a[i]              (the kernels' reciprocal, rcp_f64: binary32 seed and one
+ *                                       third-order step; within one ulp of the IEEE quotient)
  *   op 3: y[i] = fma(a[i], b[i], c[i]) (hardware fused multiply-add, reference)
- * (ops 1 and 2 are reserved).  DEVICE arrays of n doubles; c only for op 3.  Enqueued on `stream`.
+ * (op 2 is reserved).  DEVICE arrays of n doubles; b not read by op 1, c only for op 3.  Enqueued on
+ * `stream`.
  */
 TL_API tl_status tl_testing_f64_int(int op, const double *a, const double *b, const double *c, double *y, int64_t n,
                                     tl_stream stream);
 TL_API tl_status tl_testing_f32_staged_stall(const tl_dtg_in *in, const tl_dtg_out *out, int64_t n,
                                              tl_stream stream);
+/*
+ * tl_testing_pipe_rate launches `blocks` blocks of `threads` threads (a multiple of 32, at most 1024),
+ * each thread running 8 independent chains of `iters` rounds of one operation:
+ *   op 0: DFMA   op 1: DADD   op 2: DMUL   op 3: binary64 -> binary32 -> binary64 conversion pair
+ *         (two F2F and one binary32 multiply per round)   op 4: an addition written as an FMA by 1.0
+ * so that, timed by the caller, blocks x threads x 8 x iters / time is the issue rate of that
+ * operation (op 3: of conversion pairs).  `sink` is a DEVICE array of blocks x threads doubles that
+ * is never written for these operands (it only keeps the chains alive).  Enqueued on `stream`.
+ */
+TL_API tl_status tl_testing_pipe_rate(int op, int64_t iters, int32_t blocks, int32_t threads, double *sink,
+                                      tl_stream stream);
 
 #ifdef __cplusplus
 }

@@ -28,15 +28,18 @@ __device__ __forceinline__ void fwdbwd_point_f64(const FwdBwdArgs<double> &a, in
 #pragma unroll
     for (int p = 0; p < 6; ++p)
         W[p] = ld_opt(a.gout[OUT_DTG + p], x);
+    asm volatile("" ::: "memory");   // the inputs and W are loaded before any arithmetic
+
+    ChainF64Keep c;
+    chain_f64_keep<FwdBwdArgs<double>, false, true>(v, a, x, 1.0, c);
+    // the upstream gradients of Gamma are loaded only now, when the forward has released most of the
+    // inputs' registers (164 registers without spills, against 168 with spills when loaded up front:
+    // 1.78 against 1.85 ms at N = 2^22)
 #pragma unroll
     for (int k = 0; k < 3; ++k)
 #pragma unroll
         for (int p = 0; p < 6; ++p)
             V[k][p] = ld_opt(a.gout[OUT_GAMMA + 6 * k + p], x);
-    asm volatile("" ::: "memory");   // every load is issued before any arithmetic
-
-    ChainF64Keep c;
-    chain_f64_keep<FwdBwdArgs<double>, false, true>(v, a, x, 1.0, c);
 
     // ---- Eq. 5 and the footnote, reversed
     double K[6], S[6];
@@ -104,7 +107,8 @@ __device__ __forceinline__ void fwdbwd_point_f64(const FwdBwdArgs<double> &a, in
 // Block-strided with a barrier per point, like the adjoint kernels: the block's warps run the same
 // stretch of the long straight-line body together and share its instruction fetches.  The trip count
 // depends only on the block, so every thread meets every barrier.  Three 128-thread blocks per SM
-// (<= 168 registers, a few spilled): 1.85 ms at N = 2^22 against 2.12 ms at two blocks (182 registers).
+// (<= 168 registers): 1.85 ms at N = 2^22 against 2.12 ms at two blocks (182 registers), and 2.08 ms
+// at four (128 registers, 224 bytes spilled).
 template <bool kU, bool kG>
 __global__ void __launch_bounds__(kFwdBwdThreads, 3) dtg_fwdbwd_f64_kernel(const FwdBwdArgs<double> a, int64_t n)
 {

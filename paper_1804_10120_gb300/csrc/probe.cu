@@ -1,0 +1,65 @@
+// probe.cu -- issue-rate probe of the arithmetic pipes that bound the binary64 kernels (a test hook,
+// tl_testing.h).  Each thread runs eight independent dependency chains of one operation for `iters`
+// rounds, so the launch is throughput-bound on that operation's pipe once a few warps share an SM;
+// the host times it and divides the operation count by the time.  The chains' results decide a
+// store that never happens for the operands the host passes, so nothing can be removed.
+#include "tl_common.cuh"
+#include "../../include/tl_testing.h"
+
+namespace tl {
+
+constexpr int kProbeChains = 8;
+
+template <int OP>
+__global__ void __launch_bounds__(1024) pipe_rate_kernel(double *sink, int64_t iters, double a, double b)
+{
+    double v[kProbeChains];
+#pragma unroll
+    for (int k = 0; k < kProbeChains; ++k)
+        v[k] = 1.0 + 1e-3 * threadIdx.x + k;
+    const float fa = (float)a;
+    for (int64_t i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < kProbeChains; ++k) {
+            if (OP == 0)
+                v[k] = fma(v[k], a, b);                   // DFMA
+            else if (OP == 1)
+                v[k] = v[k] + b;                          // DADD
+            else if (OP == 2)
+                v[k] = v[k] * a;                          // DMUL
+            else if (OP == 3) {                           // F2F.F32.F64, FMUL, F2F.F64.F32
+                float f;
+                asm volatile("cvt.rn.f32.f64 %0, %1;" : "=f"(f) : "d"(v[k]));
+                f *= fa;
+                asm volatile("cvt.f64.f32 %0, %1;" : "=d"(v[k]) : "f"(f));
+            } else {
+                asm volatile("fma.rn.f64 %0, %1, 0d3FF0000000000000, %2;" : "=d"(v[k]) : "d"(v[k]), "d"(b));   // v*1 + b
+            }
+        }
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < kProbeChains; ++k)
+        s += v[k];
+    if (s == b * 1e300)   // false for the probe's operands (b = 0)
+        sink[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+}  // namespace tl
+
+extern "C" TL_API tl_status tl_testing_pipe_rate(int op, int64_t iters, int32_t blocks, int32_t threads, double *sink,
+                                                 tl_stream stream)
+{
+    if (op < 0 || op > 4 || iters < 0 || blocks < 1 || threads < 32 || threads > 1024 || threads % 32 || !sink)
+        return TL_ERR_INVALID_ARG;
+    const cudaStream_t s = (cudaStream_t)stream;
+    // a = 1 keeps every chain finite and exact (b = 0 for the additions); the pipe cost is the same
+    switch (op) {
+    case 0: tl::pipe_rate_kernel<0><<<blocks, threads, 0, s>>>(sink, iters, 1.0, 0.0); break;
+    case 1: tl::pipe_rate_kernel<1><<<blocks, threads, 0, s>>>(sink, iters, 1.0, 0.0); break;
+    case 2: tl::pipe_rate_kernel<2><<<blocks, threads, 0, s>>>(sink, iters, 1.0, 0.0); break;
+    case 3: tl::pipe_rate_kernel<3><<<blocks, threads, 0, s>>>(sink, iters, 1.0, 0.0); break;
+    default: tl::pipe_rate_kernel<4><<<blocks, threads, 0, s>>>(sink, iters, 1.0, 0.0); break;
+    }
+    return cudaGetLastError() == cudaSuccess ? TL_OK : TL_ERR_CUDA;
+}

@@ -173,7 +173,7 @@ tl_status launch_forward(const DeviceInfo &d, const tl_dtg_in *in, const tl_dtg_
     cudaError_t e;
     switch (dtype) {
     case TL_F64:
-        e = launch_fwd_f64(fwd_args<double>(in, out), n, shape_for(n, kFwdThreads, d.sms, d.fwd_f64_blocks), st);
+        e = launch_fwd_f64(fwd_args<double>(in, out), n, shape_for(n, kFwdF64Threads, d.sms, d.fwd_f64_blocks), st);
         break;
     case TL_F32:
         e = launch_fwd_f32_staged(fwd_args<float>(in, out), n, d.sms, shape_for(n, kFwdThreads, d.sms, d.fwd_f32_blocks),

@@ -36,6 +36,25 @@ def pointwise_floor_errors(y, y_ref, floor_frac):
     return (np.abs(y - y_ref) / den).max(axis=1)
 
 
+# Pointwise view: |y(x) - y_ref(x)| / max(|y_ref(x)|, POINTWISE_FLOOR * max|y_ref|) per component.  At
+# points where a component cancels to below the floor only an error relative to the component's scale
+# is attainable (the summands that cancel are of that scale, and each carries its own rounding), so
+# the bound is the relative error allowed at the floor: binary64 results carry errors of a few units in
+# the last place of the summands (~1e-16 of the scale), i.e. ~1e-10 at the floor; float-float pairs
+# (48 significant bits) ~1e-14 of the scale, i.e. ~1e-8.  The bounds below leave a factor ~10-100.
+POINTWISE_FLOOR = 1e-6
+POINTWISE_F64 = 1e-8
+POINTWISE_FF = 1e-6
+
+
+def assert_pointwise(y, y_ref, bound, names=OUT_NAMES, what=""):
+    errs = pointwise_floor_errors(y, y_ref, POINTWISE_FLOOR)
+    bad = [(names[c], float(errs[c])) for c in range(len(errs)) if not errs[c] <= bound]
+    assert not bad, "%s pointwise (floor %.0e of the component maximum) over %.1e: %s" % (
+        what, POINTWISE_FLOOR, bound, bad[:8])
+    return errs
+
+
 def assert_components(y, y_ref, tol, names=OUT_NAMES, what=""):
     errs = component_errors(y, y_ref)
     bad = [(names[c], float(errs[c])) for c in range(len(errs)) if not errs[c] <= tol]

@@ -62,3 +62,33 @@ def test_single_rank_is_plain_throughput():
     import bench
     t, v = bench.replica_throughput(8.0, 2 ** 24, 10, 1)
     assert t == 8.0 and v == 2 ** 24 * 10 / 8e-3
+
+
+def test_bench_gpus_flag_runs_that_many_replicas():
+    """`bench.py --gpus 2` without a launcher re-runs itself as two ranks (torch.distributed.run, gloo on
+    the CPU in launcher-check mode): rank 0 reports n_gpus = 2 and two different grids."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = {k: v for k, v in os.environ.items() if k not in ("WORLD_SIZE", "RANK", "LOCAL_RANK")}
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--gpus", "2", "--launcher-check"],
+                       capture_output=True, text=True, timeout=300, env=env)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [json.loads(s) for s in r.stdout.splitlines() if s.startswith("{")]
+    assert len(lines) == 1, r.stdout
+    line = lines[0]
+    assert line["n_gpus"] == 2 and line["gpus_arg"] == 2
+    ranks = sorted(line["ranks"], key=lambda v: v["rank"])
+    assert [v["rank"] for v in ranks] == [0, 1]
+    assert ranks[0]["seed"] != ranks[1]["seed"] and ranks[0]["grid_sha"] != ranks[1]["grid_sha"]
+
+
+def test_bench_refuses_world_size_that_contradicts_gpus():
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, WORLD_SIZE="1", RANK="0", LOCAL_RANK="0")
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--gpus", "4", "--launcher-check"],
+                       capture_output=True, text=True, timeout=120, env=env)
+    assert r.returncode == 2 and "WORLD_SIZE=1" in r.stderr

@@ -5,7 +5,7 @@ import pytest
 
 import gridgen
 import oracle
-from tests.parity import TOL_F64, assert_components, IN_NAMES
+from tests.parity import TOL_F64, POINTWISE_F64, POINTWISE_FF, assert_components, assert_pointwise, IN_NAMES
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -45,8 +45,11 @@ def test_adjoint_matches_oracle(which, dtype):
     n = 4096
     x = gridgen.random_grid(n, 3)
     gout = upstream(n, 3, which)
-    assert_components(run_bwd(x, gout, dtype), oracle.backward(x, gout), TOL_F64, names=IN_NAMES,
-                      what="adjoint %s %s" % (dtype, which))
+    g = run_bwd(x, gout, dtype)
+    ref = oracle.backward(x, gout)
+    assert_components(g, ref, TOL_F64, names=IN_NAMES, what="adjoint %s %s" % (dtype, which))
+    assert_pointwise(g, ref, POINTWISE_F64 if dtype == "f64" else POINTWISE_FF, names=IN_NAMES,
+                     what="adjoint %s %s" % (dtype, which))
 
 
 def test_ff_adjoint_special_cases():
@@ -123,6 +126,7 @@ def test_full_size_adjoint_finite_differences():
                                                             for g in gout])
     gi = gin[:, torch.from_numpy(idx).to(dev())].cpu().numpy()
     assert_components(gi, ref, TOL_F64, names=IN_NAMES, what="N=2^22 sampled adjoint")
+    assert_pointwise(gi, ref, POINTWISE_F64, names=IN_NAMES, what="N=2^22 sampled adjoint")
     gin_ff = tl.tl_dtg_backward(xd, gd, dtype="f64_ff")
     gi = gin_ff[:, torch.from_numpy(idx).to(dev())].cpu().numpy()
     assert_components(gi, ref, TOL_F64, names=IN_NAMES, what="N=2^22 sampled float-float adjoint")

@@ -64,3 +64,76 @@ def test_mul_int_equals_ieee_product():
         for a, b in operands(rng, 1 << 20):
             a, b = np.ascontiguousarray(a, np.float64), np.ascontiguousarray(b, np.float64)
             same_bits(run(0, a, b), a * b)
+
+
+def rcp_operands(rng, n):
+    """Divisors for the reciprocal: the binary32-seeded window [2^-124, 2^125) in magnitude (random
+    significands over its whole exponent range, powers of two, all-ones significands, both edges), and
+    operands just outside it and special values, which take the IEEE quotient."""
+    sign = np.where(rng.random(n) < 0.5, np.uint64(1) << np.uint64(63), np.uint64(0))
+    frac = rng.integers(0, 2**52, n, dtype=np.uint64)
+    inside = []
+    for e in (rng.integers(899, 1148, n), np.full(n, 899), np.full(n, 1147)):
+        inside.append(sign | (e.astype(np.uint64) << np.uint64(52)) | frac)
+    e = rng.integers(899, 1148, 64).astype(np.uint64) << np.uint64(52)
+    inside.append(np.concatenate([e, e | np.uint64(2**52 - 1)]))
+    inside = np.concatenate(inside).view(np.float64)
+    outside = np.concatenate([
+        (sign | (np.full(n, 898, np.uint64) << np.uint64(52)) | frac).view(np.float64),
+        (sign | (np.full(n, 1148, np.uint64) << np.uint64(52)) | frac).view(np.float64),
+        rng.integers(0, 2**64, n, dtype=np.uint64).view(np.float64),
+        np.array([0.0, -0.0, np.inf, -np.inf, np.nan, 5e-324, -2.5e-310, 2.2250738585072014e-308,
+                  1.7976931348623157e308, 2.0 ** -125, 2.0 ** 125])])
+    return inside, outside
+
+
+def in_window(d):
+    """Operands whose reciprocal takes the binary32-seeded path: biased exponent in [899, 1147]."""
+    e = (d.view(np.uint64) >> np.uint64(52)) & np.uint64(0x7ff)
+    return (e >= 899) & (e <= 1147)
+
+
+def ulp_distance(y, ref):
+    """|y - ref| in units of ref's last place, from the ordered integer images of the two values."""
+    def ordered(v):
+        b = v.view(np.int64)
+        return np.where(b < 0, np.int64(-2**63) - b, b)
+    return np.abs(ordered(y) - ordered(ref))
+
+
+def test_rcp_f64_within_one_ulp_of_ieee_quotient():
+    """The kernels' reciprocal (binary32 seed, one third-order step) is within one ulp of the host's IEEE
+    1/d everywhere in its window, and equals it bit for bit outside (where it divides)."""
+    rng = np.random.default_rng(17)
+    inside, outside = rcp_operands(rng, 1 << 20)
+    with np.errstate(all="ignore"):
+        y = run(1, inside, inside)
+        ref = 1.0 / inside
+        d = ulp_distance(y, ref)
+        assert d.max() <= 1, [(float.hex(float(inside[i])), float.hex(float(y[i]))) for i in np.argsort(d)[-3:]]
+        assert (d == 0).mean() > 0.99      # almost always the correctly rounded quotient
+        yo = run(1, outside, outside)
+        win = in_window(outside)           # random bit patterns land inside the window too
+        assert ulp_distance(yo[win], 1.0 / outside[win]).max(initial=0) <= 1
+        same_bits(yo[~win], 1.0 / outside[~win])
+
+
+def test_generated_reciprocal_within_one_ulp():
+    """The runtime generator's reciprocal (emitted as CUDA source for a scalar divisor) on the same
+    operands, through a one-statement program y = a / s with a = 1."""
+    import paper_1804_10120_gb300 as tl
+    rng = np.random.default_rng(19)
+    inside, outside = rcp_operands(rng, 1 << 18)
+    k = tl.JitKernel("in a; in s; out y; y = a / s;")
+    dev = torch.device("cuda", 0)
+    with np.errstate(all="ignore"):
+        for ops, exact in ((inside, False), (outside, True)):
+            x = np.stack([np.ones_like(ops), ops])
+            y = k.launch(torch.from_numpy(x).to(dev))
+            torch.cuda.synchronize()
+            y = y.cpu().numpy()[0]
+            win = in_window(ops)
+            assert ulp_distance(y[win], 1.0 / ops[win]).max(initial=0) <= 1
+            same_bits(y[~win], 1.0 / ops[~win])
+            assert exact or win.all()
+    k.close()

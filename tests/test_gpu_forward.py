@@ -7,7 +7,7 @@ import pytest
 
 import gridgen
 import oracle
-from tests.parity import TOL_F64, assert_components, component_errors, OUT_NAMES
+from tests.parity import TOL_F64, POINTWISE_F64, POINTWISE_FF, assert_components, assert_pointwise, component_errors, OUT_NAMES
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -38,6 +38,7 @@ def test_config0_f64_all_components():
     y = run_f64(x)
     y_ref = oracle.forward(x)
     assert_components(y, y_ref, TOL_F64, what="N=4096 seed 0 f64")
+    assert_pointwise(y, y_ref, POINTWISE_F64, what="N=4096 seed 0 f64")
 
 
 @pytest.mark.parametrize("n", [1, 2, 31, 255, 257, 4097, 100003])
@@ -102,6 +103,7 @@ def test_full_size_sampled_f64():
     ys = y[:, torch.from_numpy(idx).to(dev())].cpu().numpy()
     y_ref = oracle.forward(np.ascontiguousarray(x[:, idx]))
     assert_components(ys, y_ref, TOL_F64, what="N=2^24 sampled")
+    assert_pointwise(ys, y_ref, POINTWISE_F64, what="N=2^24 sampled")
     # every output written: no NaN / untouched memory anywhere
     assert bool(torch.isfinite(y).all())
 
@@ -182,6 +184,7 @@ def test_ff_config0_all_components():
     x = gridgen.random_grid(4096, 0)
     y = run_f64(x, dtype="f64_ff")
     assert_components(y, oracle.forward(x), TOL_F64, what="N=4096 seed 0 f64_ff")
+    assert_pointwise(y, oracle.forward(x), POINTWISE_FF, what="N=4096 seed 0 f64_ff")
 
 
 @pytest.mark.parametrize("n", [1, 33, 4099, 100003])
@@ -199,7 +202,9 @@ def test_ff_full_size_sampled():
     rng = np.random.default_rng(11)
     idx = np.unique(np.concatenate([np.arange(1024), np.arange(n - 1024, n), rng.integers(0, n, 63488)]))
     ys = y[:, torch.from_numpy(idx).to(dev())].cpu().numpy()
-    assert_components(ys, oracle.forward(np.ascontiguousarray(x[:, idx])), TOL_F64, what="ff N=2^24 sampled")
+    y_ref = oracle.forward(np.ascontiguousarray(x[:, idx]))
+    assert_components(ys, y_ref, TOL_F64, what="ff N=2^24 sampled")
+    assert_pointwise(ys, y_ref, POINTWISE_FF, what="ff N=2^24 sampled")
     assert bool(torch.isfinite(y).all())
 
 
@@ -375,3 +380,24 @@ def test_singular_metric_matches_oracle_special_values(dtype):
     y = run_f64(x, dtype=dtype)
     assert np.array_equal(np.isnan(y), np.isnan(y_ref))
     assert np.array_equal(np.isposinf(y), np.isposinf(y_ref)) and np.array_equal(np.isneginf(y), np.isneginf(y_ref))
+
+
+def test_small_grid_kernel_equals_full_kernel_bitwise():
+    """Grids of less than one block per SM run a kernel with FP64 multiplies instead of the integer-pipe
+    products; the results are the same bits.  A 4096-point grid (the small kernel) against the same
+    points repeated 16 times (65536 points: the full kernel), on random and extreme inputs."""
+    n = 4096
+    rng = np.random.default_rng(23)
+    x = gridgen.random_grid(n, 23)
+    specials = np.array([0.0, -0.0, 5e-324, 1e-160, 1e155, -7e160, np.inf, np.nan, 2.0 ** -1022])
+    pts = rng.integers(0, n, n // 4)
+    x[rng.integers(0, 43, n // 4), pts] = specials[rng.integers(0, len(specials), n // 4)]
+    with np.errstate(over="ignore"):
+        x[:, : n // 8] *= 2.0 ** rng.integers(-500, 500, n // 8)
+    y_small = run_f64(x)
+    y_full = run_f64(np.ascontiguousarray(np.tile(x, (1, 16))))
+    for k in range(16):
+        yk = y_full[:, k * n:(k + 1) * n]
+        assert np.array_equal(np.isnan(y_small), np.isnan(yk))
+        ok = np.isnan(y_small) | (y_small.view(np.uint64) == yk.view(np.uint64))
+        assert ok.all(), np.argwhere(~ok)[:5]

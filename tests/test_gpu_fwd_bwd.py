@@ -6,7 +6,7 @@ import pytest
 
 import gridgen
 import oracle
-from tests.parity import TOL_F64, assert_components, IN_NAMES
+from tests.parity import TOL_F64, POINTWISE_F64, assert_components, assert_pointwise, IN_NAMES
 from tests.test_gpu_backward import upstream
 
 torch = pytest.importorskip("torch")
@@ -86,6 +86,7 @@ def test_fused_full_size():
                           [None if g is None else np.ascontiguousarray(g[idx]) for g in gout])
     gi = gin[:, torch.from_numpy(idx).to(dev())].cpu().numpy()
     assert_components(gi, ref, TOL_F64, names=IN_NAMES, what="N=2^22 sampled fused adjoint")
+    assert_pointwise(gi, ref, POINTWISE_F64, names=IN_NAMES, what="N=2^22 sampled fused adjoint")
 
 
 def test_fused_empty_and_unsupported():
