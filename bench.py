@@ -73,8 +73,9 @@ KERNEL_SOURCES = {
     "dtg_fwd_f32_kernel": ["dtg_fwd.cu", "dtg_fwd_body.cuh", "dtg_batched.cuh"] + _COMMON,
     "dtg_fwd_f32_staged_kernel": ["dtg_fwd.cu", "dtg_fwd_body.cuh", "dtg_batched.cuh", "bulk.cuh"] + _COMMON,
     "dtg_fwd_ff_kernel": ["dtg_fwd_ff.cu", "dtg_fwd_body.cuh", "dtg_ff_body.cuh", "ff.cuh", "dtg_batched.cuh"] + _COMMON,
-    "dtg_bwd_f64_kernel": ["dtg_bwd.cu", "dtg_fwd_body.cuh", "ff.cuh"] + _COMMON,
-    "dtg_bwd_ff_kernel": ["dtg_bwd.cu", "dtg_fwd_body.cuh", "ff.cuh"] + _COMMON,
+    "dtg_bwd_f64_kernel": ["dtg_bwd.cu", "dtg_bwd_body.cuh", "dtg_fwd_body.cuh", "ff.cuh"] + _COMMON,
+    "dtg_bwd_ff_kernel": ["dtg_bwd.cu", "dtg_bwd_body.cuh", "dtg_fwd_body.cuh", "ff.cuh"] + _COMMON,
+    "dtg_fwdbwd_f64_kernel": ["dtg_fwd_bwd.cu", "dtg_bwd_body.cuh", "dtg_fwd_body.cuh"] + _COMMON,
     "dtg_batched_f64_kernel": ["dtg_fwd.cu", "dtg_fwd_body.cuh", "dtg_batched.cuh"] + _COMMON,
     "dtg_fd_kernel": ["dtg_fd.cu", "dtg_fwd_body.cuh", "dtg_ff_body.cuh", "ff.cuh"] + _COMMON,
     "tl_jit_kernel": ["jit.cu"],
@@ -321,16 +322,24 @@ def reference_arm(args):
 FLOPS_F64_PER_POINT = 197
 # Of the 197 flops, the 37 products that are not fused into an FMA run on the integer pipes (mul_int,
 # bit-identical to the FP64 multiply), and the FP64 pipe executes 71 DFMA + 18 DADD = 89 operations per
-# point.  The pipe issues DFMA and DADD at the same rate (tl_testing_pipe_rate), so the kernel's second
-# ceiling is that rate / 89 points per second.
+# point.  The pipe issues DFMA and DADD at different rates on this part (measured live by
+# tl_testing_pipe_rate: about 2.0 and 1.68 per clock per SM), so the kernel's second ceiling is the time
+# those operations take at the measured rates: n (71 / r_DFMA + 18 / r_DADD).
 FP64_OPS_PER_POINT = 89
+FWD_FP64_MIX = (71, 18)                  # (DFMA, DADD) per point, counted by ncu
 # The fused forward + adjoint for the loss sum W d_t g + V Gamma: 1192 bytes per point (43 inputs and
 # 24 upstream gradients read, 39 outputs and 43 input gradients written) and 223 FP64-pipe operations
 # (the forward's 89; Kbar/alphabar 5, betabar 15, Gammabar 18, Tbar 36, the bracket scatter 12 and the
-# folded -H A H as 2 Tbar Gamma^T 48).  The adjoint alone: 808 bytes and 181 operations; the forward
-# and the adjoint launched one after the other: 1464 bytes and 270 operations.
-FWDBWD_BYTES_PER_POINT, FWDBWD_FP64_OPS = 1192, 223
-BWD_BYTES_PER_POINT, BWD_FP64_OPS = 808, 181
+# folded -H A H as 2 Tbar Gamma^T 48): 193 DFMA + 30 DADD.  The adjoint alone: 808 bytes and 181
+# operations (163 DFMA + 18 DADD); the forward and the adjoint launched one after the other: 1464 bytes
+# and 270 operations.
+FWDBWD_BYTES_PER_POINT, FWDBWD_FP64_OPS, FWDBWD_FP64_MIX = 1192, 223, (193, 30)
+BWD_BYTES_PER_POINT, BWD_FP64_OPS, BWD_FP64_MIX = 808, 181, (163, 18)
+
+
+def fp64_floor_ms(mix, n, rates):
+    """Time the FP64 pipe needs for n points of an operation mix (DFMA, DADD) at the measured rates."""
+    return (mix[0] / rates[0] + mix[1] / rates[1]) * n * 1e3
 
 
 def device_facts(dev):
@@ -473,7 +482,36 @@ def small_grid(dev, stream):
                       "the launching stream before each launch"}
 
 
-def extras(dev, stream, steps, x64, hbm, fp64_rate=None):
+BATCH_STAGED = {"f64": [(128, 2), (128, 3), (256, 2)], "f32": [(128, 2), (128, 3), (256, 2), (256, 3), (512, 2)]}
+
+
+def batched_depths(plan, stream, steps, dtype):
+    """Best time of a batch plan at each staging depth (0: registers; 2, 3: shared memory), over the
+    block sizes provided at that depth and 1, 2 or the most blocks per SM.  Restores the plan's config."""
+    import paper_1804_10120_gb300 as tl
+    keep = plan.config, plan.points_per_thread, plan.staging
+    best = {}
+    combos = [(t, 0) for t in (128, 256, 512)] + BATCH_STAGED[dtype]
+    for threads, depth in combos:
+        plan.set_staging(0)
+        plan.set_config(threads, 1, 1)
+        if depth:
+            plan.set_staging(depth)
+        for b in (1, 2, 3, 4):
+            try:
+                plan.set_config(threads, b)
+            except tl.TLError:
+                break
+            ms = cuda_time(lambda: plan.launch(stream), max(3, steps // 2), stream)
+            if depth not in best or ms < best[depth][0]:
+                best[depth] = (ms, {"threads": threads, "blocks_per_sm": b})
+    plan.set_staging(0)
+    plan.set_config(keep[0][0], keep[0][1], keep[1])
+    plan.set_staging(keep[2])
+    return {str(k): {"ms": v[0], **v[1]} for k, v in sorted(best.items())}
+
+
+def extras(dev, stream, steps, x64, hbm, fp64_rates=None):
     """The other forms of the path, each against the plain binary64 single-grid kernel, same GPU."""
     import torch
     import gridgen
@@ -519,17 +557,22 @@ def extras(dev, stream, steps, x64, hbm, fp64_rate=None):
                   "bytes_per_point": FWDBWD_BYTES_PER_POINT,
                   "GB_s": FWDBWD_BYTES_PER_POINT * n3 / ms_fused / 1e6,
                   "hbm_frac": FWDBWD_BYTES_PER_POINT * n3 / ms_fused / 1e6 / hbm,
-                  "fp64_ops_per_point": FWDBWD_FP64_OPS,
-                  "fp64_frac": FWDBWD_FP64_OPS * n3 / (ms_fused * 1e-3) / fp64_rate if fp64_rate else None},
+                  "fp64_ops_per_point": {"DFMA": FWDBWD_FP64_MIX[0], "DADD": FWDBWD_FP64_MIX[1]},
+                  "fp64_floor_ms": fp64_floor_ms(FWDBWD_FP64_MIX, n3, fp64_rates) if fp64_rates else None,
+                  "fp64_frac": fp64_floor_ms(FWDBWD_FP64_MIX, n3, fp64_rates) / ms_fused if fp64_rates else None,
+                  "traffic": traffic_per_launch("dtg_fwdbwd_f64_kernel", n3)},
         "separate": {"ms_forward": ms_f, "ms_adjoint": ms_b, "ms": ms_fb, "points_per_s": n3 / ms_fb * 1e3,
                      "bytes_per_point": 656 + BWD_BYTES_PER_POINT, "GB_s": 1464 * n3 / ms_fb / 1e6,
                      "hbm_frac": 1464 * n3 / ms_fb / 1e6 / hbm,
                      "adjoint_hbm_frac": BWD_BYTES_PER_POINT * n3 / ms_b / 1e6 / hbm,
-                     "adjoint_fp64_frac": BWD_FP64_OPS * n3 / (ms_b * 1e-3) / fp64_rate if fp64_rate else None},
+                     "adjoint_fp64_floor_ms": fp64_floor_ms(BWD_FP64_MIX, n3, fp64_rates) if fp64_rates else None,
+                     "adjoint_fp64_frac": fp64_floor_ms(BWD_FP64_MIX, n3, fp64_rates) / ms_b if fp64_rates else None,
+                     "adjoint_traffic": traffic_per_launch("dtg_bwd_f64_kernel", n3)},
         "bytes_per_point": "fused 1192 (43 inputs + 24 upstream gradients read, 39 outputs + 43 input gradients "
                            "written); adjoint alone 808 (34 inputs: d_j beta_i is not needed, 24 upstream "
                            "gradients, 43 input gradients)",
-        "fp64_rate_source": "DFMA issue rate of tl_testing_pipe_rate, same run"}
+        "fp64_rate_source": "DFMA and DADD issue rates of tl_testing_pipe_rate, same run; frac = the time the "
+                            "kernel's DFMA + DADD mix needs at those rates / its time"}
     del x3, W, V, gout, y3, g3
     # batched: 600 subgrids n^3, n ~ U{8..48} (seed 2)
     sides = gridgen.subgrid_sides(600, 2)
@@ -558,15 +601,31 @@ def extras(dev, stream, steps, x64, hbm, fp64_rate=None):
         for xd, yd in zip(xs, ys):
             tl.tl_dtg_forward(xd, yd, stream=side_stream)
     ms_sepg = cuda_time(g2.replay, max(2, steps // 2), torch.cuda.current_stream(dev))
+    by_depth = batched_depths(plan, stream, steps, "f64")
     out["batched"] = {"workload": "600 subgrids, N_d = n^3, n ~ U{8..48} (seed 2), %d points" % tot,
                       "config": {"threads": cfg[0], "blocks_per_sm": cfg[1],
-                                 "points_per_thread": plan.points_per_thread},
+                                 "points_per_thread": plan.points_per_thread, "staging": plan.staging},
+                      "best_ms_by_staging_depth": by_depth,
                       "ms": ms_b, "points_per_s": tot / ms_b * 1e3, "GB_s": 656 * tot / ms_b / 1e6,
                       "hbm_frac": 656 * tot / ms_b / 1e6 / hbm,
                       "ms_in_graph": ms_bg,
                       "ms_600_launches": ms_sep, "ms_600_launches_in_graph": ms_sepg}
     plan.close()
+    # the same batch stored in binary32, where the single grid gains from staging
+    xs32 = [x.float() for x in xs]
+    ys32 = [torch.empty((39, x.shape[1]), dtype=torch.float32, device=dev) for x in xs]
     del xs, ys
+    plan = tl.BatchPlan(xs32, ys32, dtype="f32")
+    cfg = plan.tune(stream)
+    ms_b32 = cuda_time(lambda: plan.launch(stream), steps, stream)
+    out["batched_f32"] = {"workload": "the same 600 subgrids rounded to binary32",
+                          "config": {"threads": cfg[0], "blocks_per_sm": cfg[1],
+                                     "points_per_thread": plan.points_per_thread, "staging": plan.staging},
+                          "ms": ms_b32, "points_per_s": tot / ms_b32 * 1e3, "GB_s": 328 * tot / ms_b32 / 1e6,
+                          "hbm_frac": 328 * tot / ms_b32 / 1e6 / hbm,
+                          "best_ms_by_staging_depth": batched_depths(plan, stream, steps, "f32")}
+    plan.close()
+    del xs32, ys32
     # the chain with its 27 derivative inputs formed on the grid (periodic 256^3, 4th-order differences)
     fshape = (256, 256, 256)
     fd_fields = torch.from_numpy(gridgen.periodic_fields(fshape, 1)).to(dev)
@@ -821,15 +880,19 @@ def main():
     if variant == "f64":
         # the second ceiling of the binary64 chain: the FP64 pipe (1/64 of the FP32 rate on this part),
         # whose DFMA issue rate is measured here by the probe kernel, after the timed region
-        rate = pipe_rates(dev, stream, ops=(0,), target_ms=20.0)[0]
-        ach = FP64_OPS_PER_POINT * n / avg_launch_s
-        fp64 = {"ops_per_point": FP64_OPS_PER_POINT, "achieved_gops": ach / 1e9, "peak_gops": rate / 1e9,
-                "frac": ach / rate, "peak_source": "measured: DFMA issue rate of tl_testing_pipe_rate on this GPU, "
-                                                  "same run (8 x 256-thread blocks per SM, 8 chains per thread)",
+        r = pipe_rates(dev, stream, ops=(0, 1), target_ms=20.0)
+        rates = (r[0], r[1])
+        floor = fp64_floor_ms(FWD_FP64_MIX, n, rates)
+        fp64 = {"ops_per_point": {"DFMA": FWD_FP64_MIX[0], "DADD": FWD_FP64_MIX[1]},
+                "achieved_gops": FP64_OPS_PER_POINT * n / avg_launch_s / 1e9,
+                "peak_gops": {"DFMA": rates[0] / 1e9, "DADD": rates[1] / 1e9},
+                "floor_ms": floor, "frac": floor / (avg_launch_s * 1e3),
+                "peak_source": "measured: issue rates of tl_testing_pipe_rate on this GPU, same run (8 x 256-thread "
+                               "blocks per SM, 8 chains per thread); frac = time the 71 DFMA + 18 DADD per point need "
+                               "at those rates / the kernel's time",
                 "nominal_peak_gops": 2 * sms * max_mhz / 1e3 if max_mhz else None,
-                "nominal_source": "2 operations/clk/SM x %d SMs x %s MHz (device, nvidia-smi)" % (sms, max_mhz),
-                "floor_ms": FP64_OPS_PER_POINT * n / rate * 1e3}
-        roofline["second_ceiling"] = {"unit": "FP64 pipe operations/s", **fp64}
+                "nominal_source": "2 operations/clk/SM x %d SMs x %s MHz (device, nvidia-smi)" % (sms, max_mhz)}
+        roofline["second_ceiling"] = {"unit": "FP64 pipe", **fp64}
 
     # end to end through the host-buffer C entry point: H2D of the inputs and D2H of the outputs inside
     # the timed region, page-locked host memory
@@ -861,7 +924,7 @@ def main():
     forms = None
     if rank == 0 and world == 1 and not args.no_extras and variant != "f32" and n == N_FULL:
         forms = extras(dev, stream, max(5, min(args.steps, 20)), x, hbm,
-                       fp64["peak_gops"] * 1e9 if fp64 else None)
+                       (fp64["peak_gops"]["DFMA"] * 1e9, fp64["peak_gops"]["DADD"] * 1e9) if fp64 else None)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:

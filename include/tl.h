@@ -141,12 +141,19 @@ TL_API tl_status tl_dtg_forward_host(const tl_dtg_in *in, const tl_dtg_out *out,
  * must stay alive.  Calling it with another device current returns TL_ERR_PLAN_MISMATCH.
  *
  * tl_dtg_batched_tune times the candidate configurations (threads per block 128/256/512 x resident blocks
- * per SM x points per thread 1/2/4; a tile of a grid is threads x points-per-thread points) by launching
- * the plan on `stream` (so it writes the outputs), keeps the fastest in the plan and records it in the
- * tuning cache: the file named by TL_TUNE_CACHE, else $HOME/.cache/tl_dtg_tune.txt (TL_TUNE_CACHE=off
- * disables the cache).  It synchronises `stream`.  tl_batch_plan_config / tl_batch_plan_set_config read
- * and set threads and blocks per SM (TL_ERR_INVALID_ARG beyond the kernel's occupancy);
- * tl_batch_plan_points_per_thread / tl_batch_plan_set_points_per_thread the points per thread (1, 2 or 4).
+ * per SM x points per thread 1/2/4 x staging depth 0/2/3; a tile of a grid is threads x points-per-thread
+ * points) by launching the plan on `stream` (so it writes the outputs), keeps the fastest in the plan and
+ * records it in the tuning cache: the file named by TL_TUNE_CACHE, else $HOME/.cache/tl_dtg_tune.txt
+ * (TL_TUNE_CACHE=off disables the cache).  It synchronises `stream`.  tl_batch_plan_config /
+ * tl_batch_plan_set_config read and set threads and blocks per SM (TL_ERR_INVALID_ARG beyond the kernel's
+ * occupancy); tl_batch_plan_points_per_thread / tl_batch_plan_set_points_per_thread the points per thread
+ * (1, 2 or 4).  tl_batch_plan_staging / tl_batch_plan_set_staging read and set the staging depth: 0 loads
+ * each point's inputs straight into registers; 2 or 3 brings the input rows of each tile into shared
+ * memory by bulk copies that many tiles ahead of the arithmetic (TL_F64 and TL_F32 only, one point per
+ * thread: setting a depth sets points per thread to 1 and caps blocks per SM at what the shared memory
+ * allows; provided for binary64 128 x {2, 3} and 256 x 2 threads x depth, binary32 128 x {2, 3},
+ * 256 x {2, 3} and 512 x 2; other pairs TL_ERR_INVALID_ARG, TL_F64_FF TL_ERR_UNSUPPORTED).  Rows that do
+ * not start on a 16-byte boundary are read directly, whatever the depth.
  *
  * tl_batch_plan_check synchronises the plan's device and returns the status word recorded by its
  * launches (TL_OK, or TL_ERR_PLAN_MISMATCH if a launch found the plan inconsistent), then clears it.
@@ -160,6 +167,8 @@ TL_API tl_status tl_batch_plan_config(const tl_batch_plan *plan, int32_t *thread
 TL_API tl_status tl_batch_plan_set_config(tl_batch_plan *plan, int32_t threads, int32_t blocks_per_sm);
 TL_API tl_status tl_batch_plan_points_per_thread(const tl_batch_plan *plan, int32_t *points_per_thread);
 TL_API tl_status tl_batch_plan_set_points_per_thread(tl_batch_plan *plan, int32_t points_per_thread);
+TL_API tl_status tl_batch_plan_staging(const tl_batch_plan *plan, int32_t *stages);
+TL_API tl_status tl_batch_plan_set_staging(tl_batch_plan *plan, int32_t stages);
 TL_API tl_status tl_batch_plan_check(const tl_batch_plan *plan);
 TL_API void tl_batch_plan_destroy(tl_batch_plan *plan);
 

@@ -317,12 +317,15 @@ def _batch_lib():
         L.tl_batch_plan_set_config.argtypes = [vp, i32, i32]
         L.tl_batch_plan_points_per_thread.argtypes = [vp, ctypes.POINTER(i32)]
         L.tl_batch_plan_set_points_per_thread.argtypes = [vp, i32]
+        L.tl_batch_plan_staging.argtypes = [vp, ctypes.POINTER(i32)]
+        L.tl_batch_plan_set_staging.argtypes = [vp, i32]
         L.tl_batch_plan_check.argtypes = [vp]
         L.tl_batch_plan_destroy.argtypes = [vp]
         L.tl_batch_plan_destroy.restype = None
         for f in (L.tl_dtg_batched_prepare, L.tl_dtg_batched, L.tl_dtg_batched_tune, L.tl_batch_plan_config,
                   L.tl_batch_plan_set_config, L.tl_batch_plan_points_per_thread,
-                  L.tl_batch_plan_set_points_per_thread, L.tl_batch_plan_check):
+                  L.tl_batch_plan_set_points_per_thread, L.tl_batch_plan_check, L.tl_batch_plan_staging,
+                  L.tl_batch_plan_set_staging):
             f.restype = ctypes.c_int
         L._batch_ready = True
     return L
@@ -396,6 +399,18 @@ class BatchPlan:
         q = ctypes.c_int32()
         _check(_batch_lib().tl_batch_plan_points_per_thread(self._h, ctypes.byref(q)))
         return q.value
+
+    @property
+    def staging(self):
+        """Staging depth: 0 (inputs loaded into registers) or 2 / 3 tiles through shared memory."""
+        q = ctypes.c_int32()
+        _check(_batch_lib().tl_batch_plan_staging(self._h, ctypes.byref(q)))
+        return q.value
+
+    def set_staging(self, stages):
+        import torch
+        with torch.cuda.device(self.device):
+            _check(_batch_lib().tl_batch_plan_set_staging(self._h, stages))
 
     def check(self):
         import torch

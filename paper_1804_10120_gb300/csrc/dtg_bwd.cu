@@ -76,8 +76,9 @@ __device__ __forceinline__ void bwd_point_f64(const BwdArgs<double> &a, int64_t 
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         beta[k] = ld_stream(a.in[IN_BETA + k] + x);
+        // the sign on the integer pipe: the compiler negates a binary64 result with an FP64 addition
         st_stream(a.gin[IN_BETA + k] + x,
-                  -fma(h[sym(k, 2)], u[2], fma(h[sym(k, 1)], u[1], mul64<kIntMul>(h[sym(k, 0)], u[0]))));
+                  neg_exact(fma(h[sym(k, 2)], u[2], fma(h[sym(k, 1)], u[1], mul64<kIntMul>(h[sym(k, 0)], u[0])))));
     }
 
     // ---- Gamma: Gammabar = V - beta_k S_p

@@ -113,16 +113,20 @@ __global__ void __launch_bounds__(256, 2) dtg_fd_kernel(const FdArgs a, int64_t 
     }
 }
 
+// A block walks whole grid rows, so a block wider than a row leaves threads idle on every row: the
+// block is the row length rounded up to whole warps, at most 256 threads (128^3: 128-thread blocks,
+// four per SM, instead of 256-thread blocks with half their threads idle).
 template <int ORDER, bool FF, bool UNIFORM>
 static cudaError_t fd_launch(const FdArgs &a, int64_t n, int sms, cudaStream_t s)
 {
+    const int threads = (int)std::min<int64_t>(256, std::max<int64_t>(32, (a.nx + 31) / 32 * 32));
     int blocks = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, dtg_fd_kernel<ORDER, FF, UNIFORM>, 256, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, dtg_fd_kernel<ORDER, FF, UNIFORM>, threads, 0);
     if (e != cudaSuccess)
         return e;
     const int64_t rows = a.ny * a.nz;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(rows, (int64_t)sms * std::max(blocks, 1)));
-    dtg_fd_kernel<ORDER, FF, UNIFORM><<<grid, 256, 0, s>>>(a, n);
+    dtg_fd_kernel<ORDER, FF, UNIFORM><<<grid, threads, 0, s>>>(a, n);
     return cudaGetLastError();
 }
 

@@ -260,6 +260,197 @@ __global__ void __launch_bounds__(kThreads) dtg_batched_f32_kernel(const BatchVi
     });
 }
 
+// ---------------------------------------------------------------- batched forward, staged inputs
+// The batched loop with the 43 input rows of each tile brought into shared memory by bulk copies,
+// STAGES tiles ahead of the threads that compute on them: the staging depth, which the tuner searches
+// next to the block size and the blocks per SM (depth 0 is the register-loading kernel above).  A tile
+// is THREADS points of one grid, one per thread.  Thread 0 also produces: it walks the CTA's run of
+// tiles STAGES - 1 ahead of the others, keeping the input table of the grid it is in (and whether all
+// 43 rows start on a 16-byte boundary) in shared memory, and for each tile copies the 16-byte-aligned
+// prefix of each row, which is the whole tile unless the tile ends its grid at a byte length that is
+// not a multiple of 16.  The points beyond that prefix, and every point of a grid whose rows are not
+// 16-byte aligned, are loaded directly.  Completion is counted in bytes on one mbarrier per stage; a
+// stage with nothing to copy completes on the producer's arrival alone.  The waits are bounded as in
+// the single-grid staged kernel: a block whose wait gives up counts it (tl_wait_timeouts), lets the
+// copies it issued land (bounded again) and returns.
+template <typename T, int THREADS, int STAGES>
+__global__ void __launch_bounds__(THREADS) dtg_batched_staged_kernel(const BatchView v)
+{
+    extern __shared__ __align__(128) unsigned char staged_smem[];
+    T *const stage_buf = (T *)staged_smem;   // [STAGES][N_IN][THREADS]
+    __shared__ __align__(8) uint64_t full[STAGES];
+    __shared__ FwdArgs<T> s_args;            // consumers: table of the grid being computed
+    __shared__ const T *p_in[N_IN];          // producer: input table of the grid being copied
+    __shared__ int p_aligned;
+    const int tid = threadIdx.x;
+    const int64_t per = (v.total_tiles + gridDim.x - 1) / gridDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * per;
+    const int64_t t_end = (t0 + per < v.total_tiles) ? t0 + per : v.total_tiles;
+    if (t0 >= t_end)
+        return;
+    const int64_t count = t_end - t0;
+    int lo = 0, hi = v.G;                    // grid of tile t0: last d with tile_prefix[d] <= t0
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (v.tile_prefix[mid] <= t0)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    if (tid == 0) {
+#pragma unroll
+        for (int s = 0; s < STAGES; ++s)
+            mbar_init(&full[s], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+
+    int pd = lo, p_loaded = -1;              // producer state (thread 0 only)
+    auto issue = [&](int64_t i) {            // tile t0 + i into stage i % STAGES
+        const int64_t t = t0 + i;
+        while (pd < v.G && t >= v.tile_prefix[pd + 1])
+            ++pd;
+        const int s = (int)(i % STAGES);
+        uint32_t row = 0;
+        int64_t x0 = 0;
+        if (pd < v.G) {
+            if (pd != p_loaded) {
+                int al = 1;
+                for (int k = 0; k < N_IN; ++k) {
+                    p_in[k] = (const T *)v.tables[(int64_t)pd * (N_IN + N_OUT) + k];
+                    al &= ((uintptr_t)p_in[k] % 16 == 0) ? 1 : 0;
+                }
+                p_aligned = al;
+                p_loaded = pd;
+            }
+            x0 = (t - v.tile_prefix[pd]) * THREADS;
+            const int64_t m = (v.n[pd] - x0 < THREADS) ? v.n[pd] - x0 : THREADS;
+            row = p_aligned ? (uint32_t)(m * (int64_t)sizeof(T)) & ~15u : 0u;
+        }
+        mbar_arrive_expect_tx(&full[s], N_IN * row);
+        if (row) {
+            T *dst = stage_buf + (size_t)s * N_IN * THREADS;
+            for (int k = 0; k < N_IN; ++k)
+                bulk_copy_g2s(dst + k * THREADS, p_in[k] + x0, row, &full[s]);
+        }
+    };
+    if (tid == 0)
+        for (int64_t i = 0; i < STAGES - 1 && i < count; ++i)
+            issue(i);
+
+    int d = lo, loaded = -1, aligned = 0;
+    for (int64_t i = 0; i < count; ++i) {
+        const int64_t t = t0 + i;
+        while (d < v.G && t >= v.tile_prefix[d + 1])
+            ++d;
+        const int s = (int)(i % STAGES);
+        const bool ok = mbar_wait(&full[s], (uint32_t)((i / STAGES) & 1), kWaitPolls, kWaitNs);
+        // block-uniform; also certifies that every thread is done with tile i - 1 (its stage and table).
+        // d >= G cannot happen for a consistent plan.  Either way the block leaves once the copies it
+        // issued have landed.
+        const bool bad_plan = d >= v.G;
+        if (__syncthreads_or(!ok || bad_plan)) {
+            if (tid == 0) {
+                if (!ok)
+                    atomicAdd(&g_wait_timeouts, 1u);
+                else
+                    atomicCAS(v.status, 0u, 6u);   // TL_ERR_PLAN_MISMATCH
+                for (int64_t j = ok ? i + 1 : i; j < count && j < i + STAGES - 1; ++j)
+                    mbar_wait(&full[j % STAGES], (uint32_t)((j / STAGES) & 1), kWaitPolls, kWaitNs);
+            }
+            return;
+        }
+        if (d != loaded) {
+            bool al = true;
+            if (tid < N_IN + N_OUT) {
+                const void *q = v.tables[(int64_t)d * (N_IN + N_OUT) + tid];
+                ((const void **)&s_args)[tid] = q;
+                al = tid >= N_IN || (uintptr_t)q % 16 == 0;
+            }
+            aligned = __syncthreads_and(al);
+            loaded = d;
+        }
+        if (tid == 0 && i + STAGES - 1 < count)
+            issue(i + STAGES - 1);
+        const int64_t x0 = (t - v.tile_prefix[d]) * THREADS;
+        const int64_t m = (v.n[d] - x0 < THREADS) ? v.n[d] - x0 : THREADS;
+        const int64_t staged = aligned ? (int64_t)(((uint32_t)(m * (int64_t)sizeof(T)) & ~15u) / sizeof(T)) : 0;
+        if (tid < m) {
+            const int64_t x = x0 + tid;
+            T val[N_IN];
+            if (tid < staged) {
+                const T *src = stage_buf + (size_t)s * N_IN * THREADS + tid;
+#pragma unroll
+                for (int k = 0; k < N_IN; ++k)
+                    val[k] = src[k * THREADS];
+            } else {
+#pragma unroll
+                for (int k = 0; k < N_IN; ++k)
+                    val[k] = ld_stream(s_args.in[k] + x);
+            }
+            if constexpr (sizeof(T) == 8) {
+                chain_f64(val, s_args, x);
+            } else {
+                if (!chain_f32<true>(val, s_args, x))
+                    fwd_point_f32_general(s_args, x);
+            }
+        }
+    }
+}
+
+// Staging depths provided per element type and block size (shared memory per block <= 227 KB):
+// binary64 128 x {2, 3}, 256 x 2; binary32 128 x {2, 3}, 256 x {2, 3}, 512 x 2.
+template <typename T, int THREADS, int STAGES>
+static cudaError_t staged_kernel_op(bool launch, const BatchView *v, int grid, cudaStream_t s, int *blocks)
+{
+    const size_t smem = (size_t)STAGES * N_IN * THREADS * sizeof(T);
+    auto kern = dtg_batched_staged_kernel<T, THREADS, STAGES>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess)
+        return e;
+    if (!launch)
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kern, THREADS, smem);
+    kern<<<grid, THREADS, smem, s>>>(*v);
+    return cudaGetLastError();
+}
+
+static cudaError_t staged_dispatch(int dtype, int threads, int stages, bool launch, const BatchView *v, int grid,
+                                   cudaStream_t s, int *blocks)
+{
+    const int key = (dtype == 0 ? 0 : 1000) + threads * 10 + stages;
+    switch (key) {
+    case 1282: return staged_kernel_op<double, 128, 2>(launch, v, grid, s, blocks);
+    case 1283: return staged_kernel_op<double, 128, 3>(launch, v, grid, s, blocks);
+    case 2562: return staged_kernel_op<double, 256, 2>(launch, v, grid, s, blocks);
+    case 2282: return staged_kernel_op<float, 128, 2>(launch, v, grid, s, blocks);
+    case 2283: return staged_kernel_op<float, 128, 3>(launch, v, grid, s, blocks);
+    case 3562: return staged_kernel_op<float, 256, 2>(launch, v, grid, s, blocks);
+    case 3563: return staged_kernel_op<float, 256, 3>(launch, v, grid, s, blocks);
+    case 6122: return staged_kernel_op<float, 512, 2>(launch, v, grid, s, blocks);
+    }
+    return cudaErrorNotSupported;
+}
+
+bool batched_staging_provided(int dtype, int threads, int stages)
+{
+    if (dtype != 0 && dtype != 1)
+        return false;
+    const int key = (dtype == 0 ? 0 : 1000) + threads * 10 + stages;
+    return key == 1282 || key == 1283 || key == 2562 || key == 2282 || key == 2283 || key == 3562 || key == 3563 ||
+           key == 6122;
+}
+
+cudaError_t launch_batched_staged(int dtype, const BatchView &v, int threads, int stages, int grid, cudaStream_t s)
+{
+    return staged_dispatch(dtype, threads, stages, true, &v, grid, s, nullptr);
+}
+
+cudaError_t occupancy_batched_staged(int dtype, int threads, int stages, int *blocks)
+{
+    *blocks = 0;
+    return staged_dispatch(dtype, threads, stages, false, nullptr, 0, nullptr, blocks);
+}
+
 template <typename K> static cudaError_t launch_k(K k, const BatchView &v, int threads, int grid, cudaStream_t s)
 {
     k<<<grid, threads, 0, s>>>(v);

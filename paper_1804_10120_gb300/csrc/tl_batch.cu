@@ -38,7 +38,9 @@ int ppt_slot(int ppt)
     return -1;
 }
 
-// ---- tuning cache: one line per key, "key threads blocks_per_sm points_per_thread ms" ------------------
+constexpr int kStageOptions[3] = {0, 2, 3};   // staging depth (0: inputs loaded straight into registers)
+
+// ---- tuning cache: one line per key, "key threads blocks_per_sm points_per_thread stages ms" ----------
 std::mutex g_cache_mu;
 
 std::string cache_path()
@@ -52,7 +54,7 @@ std::string cache_path()
     return std::string(home) + "/.cache/tl_dtg_tune.txt";
 }
 
-bool cache_lookup(const std::string &key, int *threads, int *bps, int *ppt)
+bool cache_lookup(const std::string &key, int *threads, int *bps, int *ppt, int *stages)
 {
     std::lock_guard<std::mutex> lk(g_cache_mu);
     const std::string path = cache_path();
@@ -62,22 +64,23 @@ bool cache_lookup(const std::string &key, int *threads, int *bps, int *ppt)
     if (!f)
         return false;
     char line[768], k[512];
-    int t = 0, b = 0, q = 0;
+    int t = 0, b = 0, q = 0, st = 0;
     double ms = 0;
     bool found = false;
     while (fgets(line, sizeof line, f))
-        if (sscanf(line, "%511s %d %d %d %lf", k, &t, &b, &q, &ms) == 5 && key == k && thread_slot(t) >= 0 &&
-            b >= 1 && ppt_slot(q) >= 0) {
+        if (sscanf(line, "%511s %d %d %d %d %lf", k, &t, &b, &q, &st, &ms) == 6 && key == k && thread_slot(t) >= 0 &&
+            b >= 1 && ppt_slot(q) >= 0 && st >= 0) {
             *threads = t;
             *bps = b;
             *ppt = q;
+            *stages = st;
             found = true;          // the last entry for a key wins
         }
     fclose(f);
     return found;
 }
 
-void cache_store(const std::string &key, int threads, int bps, int ppt, double ms)
+void cache_store(const std::string &key, int threads, int bps, int ppt, int stages, double ms)
 {
     std::lock_guard<std::mutex> lk(g_cache_mu);
     const std::string path = cache_path();
@@ -87,7 +90,7 @@ void cache_store(const std::string &key, int threads, int bps, int ppt, double m
     if (slash != std::string::npos && slash > 0)
         mkdir(path.substr(0, slash).c_str(), 0755);   // one level; EEXIST is fine
     if (FILE *f = fopen(path.c_str(), "a")) {
-        fprintf(f, "%s %d %d %d %.6f\n", key.c_str(), threads, bps, ppt, ms);
+        fprintf(f, "%s %d %d %d %d %.6f\n", key.c_str(), threads, bps, ppt, stages, ms);
         fclose(f);
     }
 }
@@ -105,6 +108,7 @@ struct tl_batch_plan {
     int max_blocks[3] = {0, 0, 0};          // occupancy per thread option
     int threads = 256, blocks_per_sm = 0;   // launch configuration
     int ppt = 1;                            // points per thread in a tile
+    int stages = 0;                         // staging depth (0: registers; else ppt == 1)
     std::string key;                        // tuning-cache key
     // device data
     void **d_tables = nullptr;              // G x 82
@@ -239,17 +243,25 @@ tl_status tl_dtg_batched_prepare(const tl_dtg_in *in, const tl_dtg_out *out, con
     }
     // tuning-cache key: GPU, SMs, dtype, batch shape (G and the size of the batch in powers of two)
     char key[512];
-    snprintf(key, sizeof key, "%s|sm%d|dtype%d|batched2|G%d|log2pts%d", di->name, di->sms, (int)dtype, (int)G,
+    snprintf(key, sizeof key, "%s|sm%d|dtype%d|batched3|G%d|log2pts%d", di->name, di->sms, (int)dtype, (int)G,
              total > 0 ? (int)std::floor(std::log2((double)total)) : 0);
     p->key = key;
     p->threads = 256;
     p->blocks_per_sm = p->max_blocks[1];
     p->ppt = 1;
-    int t = 0, b = 0, q = 0;
-    if (cache_lookup(p->key, &t, &b, &q) && b <= p->max_blocks[thread_slot(t)]) {
-        p->threads = t;
-        p->blocks_per_sm = b;
-        p->ppt = q;
+    int t = 0, b = 0, q = 0, st = 0, sb = 0;
+    if (cache_lookup(p->key, &t, &b, &q, &st)) {
+        if (st == 0 && b <= p->max_blocks[thread_slot(t)]) {
+            p->threads = t;
+            p->blocks_per_sm = b;
+            p->ppt = q;
+        } else if (st > 0 && q == 1 && batched_staging_provided((int)dtype, t, st) &&
+                   occupancy_batched_staged((int)dtype, t, st, &sb) == cudaSuccess && b <= sb) {
+            p->threads = t;
+            p->blocks_per_sm = b;
+            p->ppt = 1;
+            p->stages = st;
+        }
     }
     p->magic = kPlanMagic;
     *plan = p;
@@ -266,7 +278,9 @@ tl_status tl_dtg_batched(const tl_batch_plan *p, tl_stream stream)
         return TL_OK;
     const int64_t want = (int64_t)p->sms * p->blocks_per_sm;
     const int grid = (int)std::max<int64_t>(1, std::min(want, p->total_tiles[slot]));
-    cudaError_t e = launch_batched((int)p->dtype, view_of(p, slot), p->threads, grid, (cudaStream_t)stream);
+    cudaError_t e = p->stages > 0 ? launch_batched_staged((int)p->dtype, view_of(p, slot), p->threads, p->stages, grid,
+                                                          (cudaStream_t)stream)
+                                  : launch_batched((int)p->dtype, view_of(p, slot), p->threads, grid, (cudaStream_t)stream);
     if (e != cudaSuccess)
         return cuda_fail(e, "batched launch");
     return TL_OK;
@@ -290,9 +304,16 @@ tl_status tl_batch_plan_set_config(tl_batch_plan *p, int32_t threads, int32_t bl
     const int slot = thread_slot(threads);
     if (slot < 0)
         return fail(TL_ERR_INVALID_ARG, "threads must be 128, 256 or 512 (got %d)", (int)threads);
-    if (blocks_per_sm < 1 || blocks_per_sm > p->max_blocks[slot])
-        return fail(TL_ERR_INVALID_ARG, "blocks_per_sm must be in [1, %d] for %d threads", p->max_blocks[slot],
-                    (int)threads);
+    int maxb = p->max_blocks[slot];
+    if (p->stages > 0) {
+        if (!batched_staging_provided((int)p->dtype, threads, p->stages))
+            return fail(TL_ERR_INVALID_ARG, "staging depth %d is not provided for %d threads", p->stages, (int)threads);
+        const cudaError_t e = occupancy_batched_staged((int)p->dtype, threads, p->stages, &maxb);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+    }
+    if (blocks_per_sm < 1 || blocks_per_sm > maxb)
+        return fail(TL_ERR_INVALID_ARG, "blocks_per_sm must be in [1, %d] for %d threads", maxb, (int)threads);
     p->threads = threads;
     p->blocks_per_sm = blocks_per_sm;
     return TL_OK;
@@ -313,7 +334,44 @@ tl_status tl_batch_plan_set_points_per_thread(tl_batch_plan *p, int32_t ppt)
         return fail(TL_ERR_PLAN_MISMATCH, "not a live batch plan");
     if (ppt_slot(ppt) < 0)
         return fail(TL_ERR_INVALID_ARG, "points per thread must be 1, 2 or 4 (got %d)", (int)ppt);
+    if (p->stages > 0 && ppt != 1)
+        return fail(TL_ERR_INVALID_ARG, "a staged plan computes one point per thread");
     p->ppt = ppt;
+    return TL_OK;
+}
+
+tl_status tl_batch_plan_staging(const tl_batch_plan *p, int32_t *stages)
+{
+    if (!p || p->magic != kPlanMagic)
+        return fail(TL_ERR_PLAN_MISMATCH, "not a live batch plan");
+    if (stages)
+        *stages = p->stages;
+    return TL_OK;
+}
+
+tl_status tl_batch_plan_set_staging(tl_batch_plan *p, int32_t stages)
+{
+    tl_status s = plan_ok(p);
+    if (s != TL_OK)
+        return s;
+    if (stages == 0) {
+        p->stages = 0;
+        p->blocks_per_sm = std::min(p->blocks_per_sm, p->max_blocks[thread_slot(p->threads)]);
+        return TL_OK;
+    }
+    if (p->dtype == TL_F64_FF)
+        return fail(TL_ERR_UNSUPPORTED, "staged inputs are provided for TL_F64 and TL_F32");
+    if (!batched_staging_provided((int)p->dtype, p->threads, stages))
+        return fail(TL_ERR_INVALID_ARG, "staging depth %d is not provided for %d threads", (int)stages, p->threads);
+    int maxb = 0;
+    const cudaError_t e = occupancy_batched_staged((int)p->dtype, p->threads, stages, &maxb);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+    if (maxb < 1)
+        return fail(TL_ERR_UNSUPPORTED, "the staged kernel does not fit on an SM");
+    p->stages = stages;
+    p->ppt = 1;
+    p->blocks_per_sm = std::max(1, std::min(p->blocks_per_sm, maxb));
     return TL_OK;
 }
 
@@ -327,19 +385,30 @@ tl_status tl_dtg_batched_tune(tl_batch_plan *p, tl_stream stream)
     cudaError_t e;
     if ((e = cudaEventCreate(&e0)) != cudaSuccess || (e = cudaEventCreate(&e1)) != cudaSuccess)
         return cuda_fail(e, "cudaEventCreate");
-    const int keep_t = p->threads, keep_b = p->blocks_per_sm, keep_q = p->ppt;
-    int best_t = keep_t, best_b = keep_b, best_q = keep_q;
+    const int keep_t = p->threads, keep_b = p->blocks_per_sm, keep_q = p->ppt, keep_s = p->stages;
+    int best_t = keep_t, best_b = keep_b, best_q = keep_q, best_s = keep_s;
     float best = 1e30f;
-    for (int j = 0; j < 9 && s == TL_OK; ++j) {
-        const int i = j / 3, T = kThreadOptions[i], Q = kPptOptions[j % 3];
-        int cands[4] = {1, 2, 4, p->max_blocks[i]};
+    // threads x points per thread x staging depth; a staged kernel computes one point per thread
+    for (int j = 0; j < 27 && s == TL_OK; ++j) {
+        const int i = j / 9, T = kThreadOptions[i], Q = kPptOptions[(j / 3) % 3], S = kStageOptions[j % 3];
+        int maxb = p->max_blocks[i];
+        if (S > 0) {
+            if (Q != 1 || !batched_staging_provided((int)p->dtype, T, S))
+                continue;
+            if ((e = occupancy_batched_staged((int)p->dtype, T, S, &maxb)) != cudaSuccess) {
+                s = cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+                break;
+            }
+        }
+        int cands[4] = {1, 2, 4, maxb};
         for (int c = 0; c < 4 && s == TL_OK; ++c) {
             const int B = cands[c];
-            if (B < 1 || B > p->max_blocks[i] || (c < 3 && B == p->max_blocks[i]))
+            if (B < 1 || B > maxb || (c < 3 && B == maxb))
                 continue;
             p->threads = T;
             p->blocks_per_sm = B;
             p->ppt = Q;
+            p->stages = S;
             if ((s = tl_dtg_batched(p, stream)) != TL_OK)   // warm-up
                 break;
             cudaEventRecord(e0, st);
@@ -357,6 +426,7 @@ tl_status tl_dtg_batched_tune(tl_batch_plan *p, tl_stream stream)
                 best_t = T;
                 best_b = B;
                 best_q = Q;
+                best_s = S;
             }
         }
     }
@@ -365,8 +435,9 @@ tl_status tl_dtg_batched_tune(tl_batch_plan *p, tl_stream stream)
     p->threads = best_t;
     p->blocks_per_sm = best_b;
     p->ppt = best_q;
+    p->stages = best_s;
     if (s == TL_OK && best < 1e30f)
-        cache_store(p->key, best_t, best_b, best_q, best / 3.0);
+        cache_store(p->key, best_t, best_b, best_q, best_s, best / 3.0);
     return s;
 }
 

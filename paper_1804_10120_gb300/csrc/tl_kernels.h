@@ -45,6 +45,12 @@ cudaError_t launch_batched(int dtype, const BatchView &v, int threads, int grid,
 // Resident blocks per SM of the batched kernel for dtype and block size.
 cudaError_t occupancy_batched(int dtype, int threads, int *blocks);
 cudaError_t launch_batched_ff(const BatchView &v, int threads, int grid, cudaStream_t s);
+// Batched forward with the inputs staged through shared memory `stages` tiles deep (tiles of `threads`
+// points, one per thread: the plan's points-per-thread-1 tiling).  dtype 0 or 1; see
+// batched_staging_provided for the (threads, stages) pairs built.
+bool batched_staging_provided(int dtype, int threads, int stages);
+cudaError_t launch_batched_staged(int dtype, const BatchView &v, int threads, int stages, int grid, cudaStream_t s);
+cudaError_t occupancy_batched_staged(int dtype, int threads, int stages, int *blocks);
 cudaError_t occupancy_batched_ff(int threads, int *blocks);
 
 // Resident blocks per SM of each kernel (0 where a kernel is not provided).

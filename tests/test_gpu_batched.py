@@ -95,8 +95,11 @@ def test_tuner_picks_a_valid_config(tmp_path, monkeypatch):
     assert t in (128, 256, 512) and b >= 1 and q in (1, 2, 4)
     text = (tmp_path / "tune.txt").read_text()
     assert "batched" in text and ("%d %d %d" % (t, b, q)) in text
+    st = plan.staging
+    assert st in (0, 2, 3) and (st == 0 or q == 1)
+    assert ("%d %d %d %d" % (t, b, q, st)) in text
     plan2 = tl.BatchPlan(xs, ys)             # same shape: configuration from the cache
-    assert plan2.config == (t, b) and plan2.points_per_thread == q
+    assert plan2.config == (t, b) and plan2.points_per_thread == q and plan2.staging == st
     plan2.launch()
     torch.cuda.synchronize()
     for x, y in zip(hosts, ys):
@@ -180,3 +183,80 @@ def test_array_and_scattered_row_tables(dtype):
                 assert torch.equal(got, r), (dtype, ppt)
         plan.check()
         plan.close()
+
+
+STAGED = {"f64": [(128, 2), (128, 3), (256, 2)], "f32": [(128, 2), (128, 3), (256, 2), (256, 3), (512, 2)]}
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_staged_inputs_every_depth_bitwise(dtype):
+    """Inputs staged through shared memory (depth 2 or 3) for every block size provided, at one and at
+    the most blocks per SM: bit for bit the single-grid result on grids whose rows start on a 16-byte
+    boundary (staged), whose rows do not (odd n in binary64 as [43, n] arrays: loaded directly), whose
+    last tile has a byte length that is not a multiple of 16 (the rest of the tile loaded directly),
+    a one-point and an empty grid; then in a CUDA graph."""
+    import paper_1804_10120_gb300 as tl
+    td = torch.float32 if dtype == "f32" else torch.float64
+    sides = [8, 9, 1, 0, 13, 16, 7, 21, 4, 11, 6]
+    hosts, xs, ys = make_batch(sides, 25, td)
+    refs = [tl.tl_dtg_forward(x, dtype=dtype) for x in xs]
+    torch.cuda.synchronize()
+    plan = tl.BatchPlan(xs, ys, dtype=dtype)
+    for threads, stages in STAGED[dtype]:
+        plan.set_staging(0)                  # the block size is checked against the current depth
+        plan.set_config(threads, 1, 1)
+        plan.set_staging(stages)
+        assert plan.staging == stages and plan.points_per_thread == 1
+        for bps in (1, 99):
+            if bps == 99:   # as many blocks per SM as the shared memory allows
+                b = 1
+                while True:
+                    try:
+                        plan.set_config(threads, b + 1)
+                    except tl.TLError:
+                        break
+                    b += 1
+                plan.set_config(threads, b)
+            for y in ys:
+                y.fill_(float("nan"))
+            plan.launch()
+            torch.cuda.synchronize()
+            for d, (y, r) in enumerate(zip(ys, refs)):
+                assert torch.equal(y, r), (dtype, threads, stages, bps, d)
+    plan.check()
+    assert tl.tl_wait_timeouts() == 0
+    for y in ys:
+        y.fill_(float("nan"))
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        plan.launch(stream=s)
+    g.replay()
+    torch.cuda.synchronize()
+    for y, r in zip(ys, refs):
+        assert torch.equal(y, r)
+    plan.set_staging(0)
+    assert plan.staging == 0
+    plan.close()
+
+
+def test_staging_rejects_what_is_not_provided():
+    import paper_1804_10120_gb300 as tl
+    hosts, xs, ys = make_batch([6, 5], 26)
+    plan = tl.BatchPlan(xs, ys)
+    plan.set_config(512, 1, 1)
+    with pytest.raises(tl.TLError) as e:
+        plan.set_staging(2)                  # 512 x 2 binary64 stages do not fit in shared memory
+    assert e.value.status == 1
+    plan.set_config(128, 1, 2)
+    plan.set_staging(3)
+    assert plan.points_per_thread == 1
+    with pytest.raises(tl.TLError):
+        plan.set_config(128, 1, 2)           # a staged plan computes one point per thread
+    plan.close()
+    plan = tl.BatchPlan(xs, ys, dtype="f64_ff")
+    with pytest.raises(tl.TLError) as e:
+        plan.set_staging(2)
+    assert e.value.status == 3
+    plan.close()
