@@ -651,6 +651,14 @@ def extras(dev, stream, steps, x64, hbm, fp64_rates=None):
                               "ms": ms_gen, "points_per_s": n / ms_gen * 1e3, "GB_s": 656 * n / ms_gen / 1e6,
                               "hbm_frac": 656 * n / ms_gen / 1e6 / hbm}
     k.close()
+    # the same chain with the footnote's sum written as a symmetric temporary (6 sums, not 9 chains)
+    from paper_1804_10120_gb300.programs import CHAIN_SYM
+    k = tl.JitKernel(CHAIN_SYM)
+    ms_sym = cuda_time(lambda: k.launch(x64, y, stream=stream), steps, stream)
+    out["generated_chain"]["symmetric_footnote_sum"] = {
+        "ms": ms_sym, "points_per_s": n / ms_sym * 1e3, "hbm_frac": 656 * n / ms_sym / 1e6 / hbm,
+        "program": "as the chain, with S(i,j) = Sum(k, Gamma(k,i,j)*beta(k)) a temporary symmetric in ij"}
+    k.close()
     # the same program unfused: one kernel per assigned tensor, then per stored component, with the
     # intermediates through device memory (the paper's evaluation model and its "Arrays" baseline)
     from paper_1804_10120_gb300.statements import StatementPipeline

@@ -42,6 +42,14 @@ TL_API tl_status tl_testing_f64_int(int op, const double *a, const double *b, co
 TL_API tl_status tl_testing_f32_staged_stall(const tl_dtg_in *in, const tl_dtg_out *out, int64_t n,
                                              tl_stream stream);
 /*
+ * tl_testing_batched_staged_stall launches a plan whose staging depth is 2 or 3 (tl_batch_plan_set_staging)
+ * once, with every stage announcing 16 bytes more than its copies deliver, so that no stage completes:
+ * each block's bounded wait runs out, the block counts it in the counter tl_wait_timeouts reads, waits
+ * (bounded again) for the stages it issued, and leaves without writing outputs.  TL_ERR_INVALID_ARG for a
+ * plan that does not stage.  Exercises the failure path of the staged batched kernel's waits.
+ */
+TL_API tl_status tl_testing_batched_staged_stall(const tl_batch_plan *plan, tl_stream stream);
+/*
  * tl_testing_pipe_rate launches `blocks` blocks of `threads` threads (a multiple of 32, at most 1024),
  * each thread running 8 independent chains of `iters` rounds of one operation:
  *   op 0: DFMA   op 1: DADD   op 2: DMUL   op 3: binary64 -> binary32 -> binary64 conversion pair

@@ -21,6 +21,8 @@ struct BatchView {
     int32_t G;
     int32_t ppt;                   // points per thread in a tile (the tile holds blockDim.x x ppt points)
     uint32_t *status;              // 0 = fine; a TL_ERR_* code if the plan looked inconsistent
+    uint32_t extra_tx;             // staged kernels: bytes announced per stage beyond the copies; 0 in use
+                                   // (a test hook sets it so that no stage completes)
 };
 
 template <typename T, typename Body>

@@ -327,7 +327,7 @@ __global__ void __launch_bounds__(THREADS) dtg_batched_staged_kernel(const Batch
             const int64_t m = (v.n[pd] - x0 < THREADS) ? v.n[pd] - x0 : THREADS;
             row = p_aligned ? (uint32_t)(m * (int64_t)sizeof(T)) & ~15u : 0u;
         }
-        mbar_arrive_expect_tx(&full[s], N_IN * row);
+        mbar_arrive_expect_tx(&full[s], N_IN * row + v.extra_tx);
         if (row) {
             T *dst = stage_buf + (size_t)s * N_IN * THREADS;
             for (int k = 0; k < N_IN; ++k)

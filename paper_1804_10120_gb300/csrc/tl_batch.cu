@@ -13,6 +13,7 @@
 
 #include "dtg_batched.cuh"
 #include "tl_host.h"
+#include "../../include/tl_testing.h"
 #include "tl_kernels.h"
 
 namespace tl {
@@ -143,6 +144,7 @@ static BatchView view_of(const tl_batch_plan *p, int slot)
     v.ppt = kPptOptions[slot % 3];
     v.G = p->G;
     v.status = p->d_status;
+    v.extra_tx = 0;
     return v;
 }
 
@@ -439,6 +441,24 @@ tl_status tl_dtg_batched_tune(tl_batch_plan *p, tl_stream stream)
     if (s == TL_OK && best < 1e30f)
         cache_store(p->key, best_t, best_b, best_q, best_s, best / 3.0);
     return s;
+}
+
+tl_status tl_testing_batched_staged_stall(const tl_batch_plan *p, tl_stream stream)
+{
+    tl_status s = plan_ok(p);
+    if (s != TL_OK)
+        return s;
+    if (p->stages == 0)
+        return fail(TL_ERR_INVALID_ARG, "the plan does not stage its inputs");
+    const int slot = thread_slot(p->threads) * 3 + ppt_slot(p->ppt);
+    if (p->total_tiles[slot] == 0)
+        return TL_OK;
+    const int64_t want = (int64_t)p->sms * p->blocks_per_sm;
+    const int grid = (int)std::max<int64_t>(1, std::min(want, p->total_tiles[slot]));
+    BatchView v = view_of(p, slot);
+    v.extra_tx = 16;
+    const cudaError_t e = launch_batched_staged((int)p->dtype, v, p->threads, p->stages, grid, (cudaStream_t)stream);
+    return e == cudaSuccess ? TL_OK : cuda_fail(e, "staged batched launch");
 }
 
 tl_status tl_batch_plan_check(const tl_batch_plan *p)

@@ -154,6 +154,7 @@ extern "C" TL_API tl_status tl_dtg_batched_noalloc(const tl_dtg_in *in, const tl
     v.ppt = 1;
     v.G = G;
     v.status = (uint32_t *)(dsc + kStatusOffset);
+    v.extra_tx = 0;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)D.sms * D.blocks[dtype], tiles));
     if ((e = launch_batched((int)dtype, v, kNoAllocThreads, grid, st)) != cudaSuccess)
         return cuda_fail(e, "allocation-free batched launch");

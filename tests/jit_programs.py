@@ -1,11 +1,12 @@
 """Tensor-index programs shared by the generator tests (plain text; no arithmetic here).  "chain" is
 the package's own program, the one the benchmark compiles; the interpreter pins check it against the
 chain oracle."""
-from paper_1804_10120_gb300.programs import CHAIN
+from paper_1804_10120_gb300.programs import CHAIN, CHAIN_SYM
 from tests.test_tensor_expr_oracle import EXPR_PROGRAMS
 
 PROGRAMS = {
     "chain": CHAIN,
+    "chain_sym": CHAIN_SYM,
     "eq9": EXPR_PROGRAMS[9],
     "eq14": EXPR_PROGRAMS[14],
     "eq17": EXPR_PROGRAMS[17],

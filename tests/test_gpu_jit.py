@@ -23,7 +23,7 @@ def test_generated_kernel_matches_interpreter(name, n):
     import paper_1804_10120_gb300 as tl
     k = tl.JitKernel(PROGRAMS[name])
     p = Program(PROGRAMS[name])
-    if name == "chain":
+    if name.startswith("chain"):
         x = gridgen.random_grid(n, 71)
     else:
         x = gridgen.normal_fields(k.n_in, n, 71, 6000)
@@ -33,7 +33,7 @@ def test_generated_kernel_matches_interpreter(name, n):
     ref = p.run(x)
     # generated code may contract a*b + c into an FMA: compare per component against the
     # component's scale (1e-12 for the chain, the 43-input program with a division)
-    tol = TOL_F64 if name == "chain" else 1e-13
+    tol = TOL_F64 if name.startswith("chain") else 1e-13
     assert component_errors(y, ref).max() <= tol, name
     k.close()
 
@@ -79,7 +79,7 @@ def test_unfused_pipeline_matches_fused_and_interpreter(mode, name):
     from paper_1804_10120_gb300.statements import StatementPipeline
     n = 65537
     pl = StatementPipeline(PROGRAMS[name], mode)
-    x = gridgen.random_grid(n, 72) if name == "chain" else gridgen.normal_fields(pl.n_in, n, 72, 6000)
+    x = gridgen.random_grid(n, 72) if name.startswith("chain") else gridgen.normal_fields(pl.n_in, n, 72, 6000)
     xd = torch.from_numpy(x).to(dev())
     s = torch.cuda.Stream()
     s.wait_stream(torch.cuda.current_stream())
@@ -87,7 +87,7 @@ def test_unfused_pipeline_matches_fused_and_interpreter(mode, name):
     s.synchronize()
     y_fused = pl.fused.launch(xd)
     torch.cuda.synchronize()
-    tol = TOL_F64 if name == "chain" else 1e-13
+    tol = TOL_F64 if name.startswith("chain") else 1e-13
     ref = Program(PROGRAMS[name]).run(x)
     assert component_errors(y_st.cpu().numpy(), ref).max() <= tol, name
     assert component_errors(y_st.cpu().numpy(), y_fused.cpu().numpy()).max() <= tol, name
@@ -125,4 +125,26 @@ def test_generated_chain_emits_fused_contractions():
     y_hand = tl.tl_dtg_forward(xd)
     torch.cuda.synchronize()
     assert component_errors(y_gen.cpu().numpy(), y_hand.cpu().numpy()).max() <= TOL_F64
+    k.close()
+
+
+def test_generated_chain_with_symmetric_footnote_sum():
+    """With the footnote's sum written as a temporary symmetric in ij, the generator forms its 6 distinct
+    values (one integer-pipe product and 2 FMAs each, then 9 subtractions: 21 FP64 operations) instead
+    of 9 chains of 3 FMAs from d_j beta_i (27), as the hand kernel does: 6 more stand-alone products
+    than the literal chain, the same outputs within the binary64 gate."""
+    import paper_1804_10120_gb300 as tl
+    from paper_1804_10120_gb300.programs import CHAIN_SYM
+    k = tl.JitKernel(CHAIN_SYM)
+    body = k.source[k.source.index("tl_jit_kernel"):]
+    assert body.count("tl_mul(") == 31 + 6 and body.count("tl_rcp(") == 1
+    x = gridgen.random_grid(100003, 6)
+    xd = torch.from_numpy(x).to(dev())
+    y_gen = k.launch(xd)
+    y_hand = tl.tl_dtg_forward(xd)
+    torch.cuda.synchronize()
+    assert component_errors(y_gen.cpu().numpy(), y_hand.cpu().numpy()).max() <= TOL_F64
+    idx = np.arange(0, 100003, 7)
+    assert_components(y_gen.cpu().numpy()[:, idx], oracle.forward(np.ascontiguousarray(x[:, idx])), TOL_F64,
+                      what="symmetric-sum chain")
     k.close()

@@ -57,3 +57,38 @@ def test_stall_hook_rejects_unaligned_inputs():
     L.tl_testing_f32_staged_stall.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]
     L.tl_testing_f32_staged_stall.restype = ctypes.c_int
     assert L.tl_testing_f32_staged_stall(ctypes.byref(itab), ctypes.byref(otab), n, tl._stream_handle(None, dev)) == 2
+
+
+def test_staged_batched_waits_give_up_and_leave_outputs_untouched():
+    """The staged batched kernel's waits on its bulk copies are bounded as well: with every stage
+    announcing 16 bytes that never arrive, each block gives up, counts it, lets its copies land and
+    leaves; nothing is written, and the next normal launch of the same plan is correct."""
+    import paper_1804_10120_gb300 as tl
+    from tests.test_gpu_batched import make_batch
+    hosts, xs, ys = make_batch([8, 12, 6], 27)
+    plan = tl.BatchPlan(xs, ys)
+    plan.set_config(128, 1, 1)
+    plan.set_staging(2)
+    L = tl.lib()
+    L.tl_testing_batched_staged_stall.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    L.tl_testing_batched_staged_stall.restype = ctypes.c_int
+    dev = torch.device("cuda", 0)
+    tiles = sum((x.shape[1] + 127) // 128 for x in xs)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    blocks = min(tiles, sms)
+    before = tl.tl_wait_timeouts()
+    t0 = time.time()
+    tl._check(L.tl_testing_batched_staged_stall(plan._h, tl._stream_handle(None, dev)))
+    torch.cuda.synchronize()
+    assert time.time() - t0 < 10.0
+    assert tl.tl_wait_timeouts() - before == blocks
+    assert all(bool(torch.isnan(y).all()) for y in ys)
+    plan.launch()
+    torch.cuda.synchronize()
+    for x, y in zip(xs, ys):
+        assert torch.equal(tl.tl_dtg_forward(x), y)
+    plan.check()
+    plan.set_staging(0)
+    with pytest.raises(tl.TLError):
+        tl._check(L.tl_testing_batched_staged_stall(plan._h, tl._stream_handle(None, dev)))
+    plan.close()

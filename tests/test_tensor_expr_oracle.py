@@ -37,10 +37,11 @@ EXPR_PROGRAMS = {
 }
 
 
-@pytest.mark.parametrize("which", ["transcribed here", "shipped with the package"])
+@pytest.mark.parametrize("which", ["transcribed here", "shipped with the package", "symmetric footnote sum"])
 def test_chain_program_equals_chain_oracle(which):
-    from paper_1804_10120_gb300.programs import CHAIN as PACKAGE_CHAIN
-    p = Program(CHAIN if which == "transcribed here" else PACKAGE_CHAIN)
+    from paper_1804_10120_gb300.programs import CHAIN as PACKAGE_CHAIN, CHAIN_SYM
+    p = Program({"transcribed here": CHAIN, "shipped with the package": PACKAGE_CHAIN,
+                 "symmetric footnote sum": CHAIN_SYM}[which])
     assert len(p.inputs()) == 43 and len(p.outputs()) == 39
     x = gridgen.random_grid(2000, 13)
     y = p.run(x)
