@@ -82,15 +82,24 @@ KERNEL_SOURCES = {
 }
 
 
+def _code_only(text):
+    """C/CUDA source without comments and with whitespace collapsed: what the compiler sees."""
+    import re
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def src_digest(kernel=None):
-    """Digest of a kernel's source files (all kernel sources when kernel is None)."""
+    """Digest of a kernel's source files, comments and layout ignored (all kernel sources when kernel is
+    None)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1804_10120_gb300", "csrc")
     names = sorted(KERNEL_SOURCES[kernel]) if kernel else sorted(
         n for n in os.listdir(csrc) if n.endswith((".cu", ".cuh", ".h")))
     for name in names:
-        with open(os.path.join(csrc, name), "rb") as f:
-            h.update(name.encode() + f.read())
+        with open(os.path.join(csrc, name), encoding="utf-8") as f:
+            h.update(name.encode() + _code_only(f.read()).encode())
     return h.hexdigest()[:16]
 
 

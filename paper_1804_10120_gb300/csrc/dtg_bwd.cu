@@ -121,8 +121,8 @@ __device__ __forceinline__ void bwd_point_f64(const BwdArgs<double> &a, int64_t 
 }
 
 // ------------------------------------------------------------------------------ float-float adjoint
-// The binary64 adjoint needs ~270 binary64 operations per point (204 of them on the 1/64-rate FP64
-// pipe once its 68 stand-alone products run on the integer pipes).  Here the
+// The binary64 adjoint needs 240 binary64 operations per point (181 of them on the 1/64-rate FP64
+// pipe once its 59 stand-alone products run on the integer pipes).  Here the
 // inverse, the bracket, Kbar, abar and the folds of the upstream gradients stay in binary64, and every
 // contraction -- betabar, Gammabar, Hbar, Tbar, the bracket's scatter onto d_k g_ij and -H A H --
 // runs in float-float pairs (ff.cuh); points with values the pairs cannot carry take the
@@ -363,7 +363,7 @@ __global__ void __launch_bounds__(kBwdFfThreads) dtg_bwd_ff_kernel(const BwdArgs
     }
 }
 
-// Block-strided with a barrier per point, like the float-float adjoint (1.70 -> 1.68 ms at N = 2^22).
+// Block-strided with a barrier per point, like the float-float adjoint (about 1 % over a grid stride).
 // Four 128-thread blocks per SM (128 registers, 48 bytes spilled): 1.47 -> 1.40 ms at N = 2^22 against
 // three blocks at 162 registers.
 template <bool kU, bool kG>

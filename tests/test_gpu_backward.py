@@ -178,7 +178,7 @@ def test_autograd_gradcheck_small():
 
 @pytest.mark.parametrize("which", [("gamma", "dtg"), ("ginv", "gamma", "dbcov", "dtg")])
 def test_integer_pipe_products_equal_fp64_products_on_extreme_values(which):
-    """The binary64 adjoint forms its 68 stand-alone products on the integer pipes; the float-float
+    """The binary64 adjoint forms its 59 stand-alone products on the integer pipes; the float-float
     adjoint's fallback evaluates the same reverse pass with FP64 multiplies and is taken at every
     point when beta_0 = 1e30.  On inputs and upstream gradients full of zeros, subnormals, huge values,
     infinities and NaNs the two agree bit for bit."""
