@@ -491,6 +491,17 @@ def small_grid(dev, stream):
                       "the launching stream before each launch"}
 
 
+def padded_rows(host, dev, row_bytes=256):
+    """The rows of a [c, n] host tensor copied into a device buffer whose rows are padded to a multiple
+    of row_bytes; returns the c row views (length n each)."""
+    import torch
+    c, n = host.shape
+    per = max(1, row_bytes // host.element_size())
+    buf = torch.empty((c, (n + per - 1) // per * per), dtype=host.dtype, device=dev)
+    buf[:, :n].copy_(host)
+    return [buf[k, :n] for k in range(c)]
+
+
 BATCH_STAGED = {"f64": [(128, 2), (128, 3), (256, 2)], "f32": [(128, 2), (128, 3), (256, 2), (256, 3), (512, 2)]}
 
 
@@ -584,12 +595,13 @@ def extras(dev, stream, steps, x64, hbm, fp64_rates=None):
                             "kernel's DFMA + DADD mix needs at those rates / its time"}
     del x3, W, V, gout, y3, g3
     # batched: 600 subgrids n^3, n ~ U{8..48} (seed 2)
+    # each subgrid's 43 input and 39 output arrays are rows of one buffer whose row length is rounded up
+    # to 256 bytes, so that every array starts on a 32-byte sector (the padding is never read)
     sides = gridgen.subgrid_sides(600, 2)
     xs, ys = [], []
     for d, side in enumerate(sides):
-        nd = side ** 3
-        xs.append(torch.from_numpy(gridgen.random_grid(nd, 2, stream_base=gridgen.STREAMS_PER_FIELD * d)).to(dev))
-        ys.append(torch.empty((39, nd), dtype=torch.float64, device=dev))
+        xs.append(padded_rows(torch.from_numpy(gridgen.random_grid(side ** 3, 2, stream_base=gridgen.STREAMS_PER_FIELD * d)), dev))
+        ys.append(padded_rows(torch.empty((39, side ** 3), dtype=torch.float64), dev))
     tot = sum(side ** 3 for side in sides)
     plan = tl.BatchPlan(xs, ys)
     cfg = plan.tune(stream)
@@ -611,7 +623,8 @@ def extras(dev, stream, steps, x64, hbm, fp64_rates=None):
             tl.tl_dtg_forward(xd, yd, stream=side_stream)
     ms_sepg = cuda_time(g2.replay, max(2, steps // 2), torch.cuda.current_stream(dev))
     by_depth = batched_depths(plan, stream, steps, "f64")
-    out["batched"] = {"workload": "600 subgrids, N_d = n^3, n ~ U{8..48} (seed 2), %d points" % tot,
+    out["batched"] = {"workload": "600 subgrids, N_d = n^3, n ~ U{8..48} (seed 2), %d points; each subgrid's "
+                                  "arrays are rows of one buffer padded to 256-byte rows" % tot,
                       "config": {"threads": cfg[0], "blocks_per_sm": cfg[1],
                                  "points_per_thread": plan.points_per_thread, "staging": plan.staging},
                       "best_ms_by_staging_depth": by_depth,
@@ -621,8 +634,8 @@ def extras(dev, stream, steps, x64, hbm, fp64_rates=None):
                       "ms_600_launches": ms_sep, "ms_600_launches_in_graph": ms_sepg}
     plan.close()
     # the same batch stored in binary32, where the single grid gains from staging
-    xs32 = [x.float() for x in xs]
-    ys32 = [torch.empty((39, x.shape[1]), dtype=torch.float32, device=dev) for x in xs]
+    xs32 = [padded_rows(torch.stack(x).float(), dev) for x in xs]
+    ys32 = [padded_rows(torch.empty((39, x[0].shape[0]), dtype=torch.float32), dev) for x in xs]
     del xs, ys
     plan = tl.BatchPlan(xs32, ys32, dtype="f32")
     cfg = plan.tune(stream)
@@ -753,8 +766,8 @@ def only_form(args):
         sides = gridgen.subgrid_sides(args.grids, 2)
         xs, ys = [], []
         for d, side in enumerate(sides):
-            xs.append(torch.from_numpy(gridgen.random_grid(side ** 3, 2, stream_base=gridgen.STREAMS_PER_FIELD * d)).to(dev))
-            ys.append(torch.empty((39, side ** 3), dtype=torch.float64, device=dev))
+            xs.append(padded_rows(torch.from_numpy(gridgen.random_grid(side ** 3, 2, stream_base=gridgen.STREAMS_PER_FIELD * d)), dev))
+            ys.append(padded_rows(torch.empty((39, side ** 3), dtype=torch.float64), dev))
         plan = tl.BatchPlan(xs, ys, dtype=args.variant if args.variant != "f32" else "f64")
         fn = lambda: plan.launch(stream)
         units = sum(side ** 3 for side in sides)

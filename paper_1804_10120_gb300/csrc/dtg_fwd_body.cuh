@@ -53,17 +53,25 @@ struct ChainF64Keep {
     double ginv[6], h[6], T[3][6], gam[3][6];
 };
 
-// The chain on one point's 43 input values (already in registers, in the input-table order); the 39
-// outputs go to o.out[s][x] (o: any argument block with an `out` table) and the intermediates to k.
+// The chain on one point's 43 input values (in registers, in the input-table order); the 39 outputs go
+// to o.out[s][x] (o: any argument block with an `out` table) and the intermediates to k.  kLate: the
+// entries of v from K_ij on (K, alpha, beta, d_j beta_i: 19 values that only steps 3 and 4 use) are
+// not yet loaded; they are read from o.in[s][x] just before step 3, so their registers are free while
+// the inverse and Eq. 6 are formed (the caller has prefetched them into L1).
 // kScaled: the d_k g_ij and d_j beta_i entries of v are differences that still need one common factor
 // sd (a finite-difference stencil on a grid with equal spacings); sd is then applied once to
 // 1/2 g^il and fused into nabla_j beta_i instead of to each of the 27 derivatives.  kIntMul: the 37
 // products that are not fused into an FMA go to the integer pipes (mul_int); the results are the same
 // bits either way.
-template <class OutTable, bool kScaled = false, bool kIntMul = true>
-__device__ __forceinline__ void chain_f64_keep(const double (&v)[N_IN], const OutTable &o, int64_t x, double sd,
+template <class OutTable, bool kScaled = false, bool kIntMul = true, bool kLate = false>
+__device__ __forceinline__ void chain_f64_keep(const double (&v0)[N_IN], const OutTable &o, int64_t x, double sd,
                                                ChainF64Keep &k)
 {
+    double vl[N_IN];
+#pragma unroll
+    for (int s = 0; s < N_IN; ++s)
+        vl[s] = v0[s];
+    const double (&v)[N_IN] = vl;
     // step 1: inverse metric by cofactors; det by first-row expansion
     const double g00 = v[IN_G + 0], g01 = v[IN_G + 1],
                  g02 = v[IN_G + 2], g11 = v[IN_G + 3],
@@ -109,6 +117,12 @@ __device__ __forceinline__ void chain_f64_keep(const double (&v)[N_IN], const Ou
             k.gam[i][p] = gam[i][p];
         }
 
+    if constexpr (kLate) {
+        asm volatile("" ::: "memory");   // the late inputs are loaded here, not hoisted above Eq. 6
+#pragma unroll
+        for (int s = IN_K; s < N_IN; ++s)
+            vl[s] = ld_stream(o.in[s] + x);
+    }
     // step 3: nabla_j beta_i = d_j beta_i - Gamma^k_ij beta_k.  Gamma^k_ij beta_k is symmetric in ij, so
     // its 6 distinct sums are formed once (a product and 2 FMAs each) and subtracted from the 9
     // derivatives: 21 FP64-pipe operations instead of the 27 FMAs of 9 separate chains.
@@ -152,14 +166,24 @@ __device__ __forceinline__ void chain_f64(const double (&v)[N_IN], const OutTabl
     chain_f64_keep<OutTable, kScaled, kIntMul>(v, o, x, sd, unused);
 }
 
+// One point of the forward.  The 24 inputs of the inverse and Eq. 6 (g_ij, d_k g_ij) are loaded before
+// any arithmetic; the other 19 are prefetched into L1 and loaded before step 3, which leaves room for
+// three 256-thread blocks per SM (80 registers, 24 warps): 2.77 -> 2.75 ms at N = 2^24 against every
+// input loaded up front at two blocks (128 registers).
 template <bool kIntMul = true> __device__ __forceinline__ void fwd_point_f64(const FwdArgs<double> &a, int64_t x)
 {
     double v[N_IN];
 #pragma unroll
-    for (int s = 0; s < N_IN; ++s)
+    for (int s = 0; s < IN_K; ++s)
         v[s] = ld_stream(a.in[s] + x);
-    asm volatile("" ::: "memory");   // every load is issued before any arithmetic
-    chain_f64<FwdArgs<double>, false, kIntMul>(v, a, x);
+#pragma unroll
+    for (int s = IN_K; s < N_IN; ++s) {
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(a.in[s] + x));
+        v[s] = 0.0;
+    }
+    asm volatile("" ::: "memory");   // the first 24 loads are issued before any arithmetic
+    ChainF64Keep unused;
+    chain_f64_keep<FwdArgs<double>, false, kIntMul, true>(v, a, x, 1.0, unused);
 }
 
 }  // namespace tl

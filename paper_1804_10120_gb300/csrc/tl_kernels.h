@@ -8,7 +8,7 @@ namespace tl {
 
 constexpr int kFwdThreads = 256;
 // The binary64 forward kernel (dtg_fwd_f64_kernel): threads per block and blocks per SM it is built for.
-constexpr int kFwdF64Threads = 256, kFwdF64Blocks = 2;
+constexpr int kFwdF64Threads = 256, kFwdF64Blocks = 3;
 
 // Grid and block size of a one-dimensional launch.
 struct LaunchShape {
