@@ -148,3 +148,18 @@ def test_bench_traffic_is_tied_to_kernel_sources(monkeypatch, tmp_path):
     monkeypatch.setattr(bench, "src_digest", lambda k=None: "changed")
     assert bench.traffic_per_launch(kernel, 1 << 24) is None
     assert bench.traffic_per_launch("no_such_kernel", 1 << 24) is None
+
+
+def test_pipe_rate_probe_argument_checks(L):
+    """The FP64 pipe-rate probe hook rejects bad arguments on the host, before any launch."""
+    f = L.tl_testing_pipe_rate
+    f.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    sink = ctypes.c_void_p(1 << 20)
+    assert f(5, 16, 1, 256, sink, None) == 1          # no such operation
+    assert f(-1, 16, 1, 256, sink, None) == 1
+    assert f(0, -1, 1, 256, sink, None) == 1          # negative rounds
+    assert f(0, 16, 0, 256, sink, None) == 1          # no blocks
+    assert f(0, 16, 1, 33, sink, None) == 1           # not whole warps
+    assert f(0, 16, 1, 2048, sink, None) == 1         # beyond 1024 threads
+    assert f(0, 16, 1, 256, None, None) == 1          # no sink

@@ -137,3 +137,32 @@ def test_generated_reciprocal_within_one_ulp():
             same_bits(y[~win], 1.0 / ops[~win])
             assert exact or win.all()
     k.close()
+
+
+def test_pipe_rate_probe_runs_and_writes_nothing():
+    """Every operation of the FP64 pipe-rate probe launches, finishes, and leaves its sink unwritten (the
+    chains only decide a store that the probe's operands never trigger); the DFMA rate comes out in
+    the range two operations per clock per SM allows."""
+    import paper_1804_10120_gb300 as tl
+    dev = torch.device("cuda", 0)
+    L = tl.lib()
+    L.tl_testing_pipe_rate.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                       ctypes.c_void_p, ctypes.c_void_p]
+    L.tl_testing_pipe_rate.restype = ctypes.c_int
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    blocks, threads = 8 * sms, 256
+    sink = torch.full((blocks * threads,), float("nan"), dtype=torch.float64, device=dev)
+    st = torch.cuda.current_stream(dev)
+    for op in range(5):
+        assert L.tl_testing_pipe_rate(op, 64, blocks, threads, sink.data_ptr(), st.cuda_stream) == 0
+    torch.cuda.synchronize()
+    assert bool(torch.isnan(sink).all())
+    iters = 4096
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    assert L.tl_testing_pipe_rate(0, iters, blocks, threads, sink.data_ptr(), st.cuda_stream) == 0
+    e1.record(st)
+    torch.cuda.synchronize()
+    per_s = blocks * threads * 8 * iters / (e0.elapsed_time(e1) * 1e-3)
+    per_clk_sm = per_s / (sms * 2.07e9)                # at the highest SM clock of the part
+    assert 0.5 < per_clk_sm < 2.2, per_clk_sm
