@@ -136,3 +136,33 @@ def test_fused_in_cuda_graph_and_with_scattered_tables():
     graph.replay()
     torch.cuda.synchronize()
     assert torch.equal(y, y_ref) and torch.equal(g, g_ref)
+
+
+def test_fused_on_extreme_values():
+    """Inputs and upstream gradients full of zeros, subnormals, huge values, infinities and NaNs on some
+    points: the fused kernel's outputs stay bit for bit those of the forward kernel (the same body, its
+    integer-pipe products falling back to the FP64 multiply where they must), and on the points left
+    untouched the gradients still meet the oracle's gate."""
+    import paper_1804_10120_gb300 as tl
+    n = 1 << 14
+    rng = np.random.default_rng(33)
+    x = gridgen.random_grid(n, 33)
+    gout = upstream(n, 34, ("ginv", "gamma", "dbcov", "dtg"))
+    specials = np.array([0.0, -0.0, 5e-324, -2.5e-310, 1e-160, 1e155, -7e160, 1e300, np.inf, -np.inf, np.nan])
+    hit = np.zeros(n, dtype=bool)
+    pts = rng.integers(0, n // 2, n // 4)
+    x[rng.integers(0, 43, n // 4), pts] = specials[rng.integers(0, len(specials), n // 4)]
+    hit[pts] = True
+    for g in gout:
+        k = rng.integers(0, n // 2, n // 32)
+        g[k] = specials[rng.integers(0, len(specials), n // 32)]
+        hit[k] = True
+    with np.errstate(all="ignore"):
+        y, gin, y_sep = run_fused(x, gout)
+    assert np.array_equal(np.isnan(y), np.isnan(y_sep))
+    ok = np.isnan(y) | (y.view(np.uint64) == y_sep.view(np.uint64))
+    assert ok.all(), np.argwhere(~ok)[:5]
+    clean = np.nonzero(~hit)[0]
+    assert clean.size > n // 3
+    ref = oracle.backward(np.ascontiguousarray(x[:, clean]), [np.ascontiguousarray(g[clean]) for g in gout])
+    assert_components(gin[:, clean], ref, TOL_F64, names=IN_NAMES, what="fused, untouched points")
