@@ -75,7 +75,10 @@ KERNEL_SOURCES = {
     "dtg_fwd_ff_kernel": ["dtg_fwd_ff.cu", "dtg_fwd_body.cuh", "dtg_ff_body.cuh", "ff.cuh", "dtg_batched.cuh"] + _COMMON,
     "dtg_bwd_f64_kernel": ["dtg_bwd.cu", "dtg_bwd_body.cuh", "dtg_fwd_body.cuh", "ff.cuh"] + _COMMON,
     "dtg_bwd_ff_kernel": ["dtg_bwd.cu", "dtg_bwd_body.cuh", "dtg_fwd_body.cuh", "ff.cuh"] + _COMMON,
-    "dtg_fwdbwd_f64_kernel": ["dtg_fwd_bwd.cu", "dtg_bwd_body.cuh", "dtg_fwd_body.cuh"] + _COMMON,
+    "dtg_fwdbwd_f64_kernel": ["dtg_fwd_bwd.cu", "dtg_bwd_body.cuh", "dtg_fwd_body.cuh", "dtg_ff_body.cuh", "ff.cuh"]
+    + _COMMON,
+    "dtg_fwdbwd_ff_kernel": ["dtg_fwd_bwd.cu", "dtg_bwd_body.cuh", "dtg_fwd_body.cuh", "dtg_ff_body.cuh", "ff.cuh"]
+    + _COMMON,
     "dtg_batched_f64_kernel": ["dtg_fwd.cu", "dtg_fwd_body.cuh", "dtg_batched.cuh"] + _COMMON,
     "dtg_fd_kernel": ["dtg_fd.cu", "dtg_fwd_body.cuh", "dtg_ff_body.cuh", "ff.cuh"] + _COMMON,
     "tl_jit_kernel": ["jit.cu"],
@@ -567,7 +570,11 @@ def extras(dev, stream, steps, x64, hbm, fp64_rates=None):
                                   tl.tl_dtg_backward(x3, gout, g3, dtype="f64_ff", stream=stream)), steps, stream)
     ms_b_ff = cuda_time(lambda: tl.tl_dtg_backward(x3, gout, g3, dtype="f64_ff", stream=stream), steps, stream)
     ms_fused = cuda_time(lambda: tl.tl_dtg_forward_backward(x3, gout, y3, g3, stream=stream), steps, stream)
+    ms_fused_ff = cuda_time(lambda: tl.tl_dtg_forward_backward(x3, gout, y3, g3, dtype="f64_ff", stream=stream),
+                            steps, stream)
     out["fwd_adjoint_ff"] = {"workload": "N=2^22, seed 3, L = sum W dtg + V Gamma", "ms_adjoint": ms_b_ff,
+                             "fused_ms": ms_fused_ff, "fused_points_per_s": n3 / ms_fused_ff * 1e3,
+                             "fused_hbm_frac": FWDBWD_BYTES_PER_POINT * n3 / ms_fused_ff / 1e6 / hbm,
                              "ms": ms_fb_ff, "points_per_s": n3 / ms_fb_ff * 1e3, "GB_s": 1464 * n3 / ms_fb_ff / 1e6,
                              "hbm_frac": 1464 * n3 / ms_fb_ff / 1e6 / hbm,
                              "arith": "float-float forward and adjoint (binary64 inverse, bracket, folds)"}
@@ -744,7 +751,8 @@ def only_form(args):
         gout = [None] * 6 + [V[i] for i in range(18)] + [None] * 9 + [W[i] for i in range(6)]
         y = torch.empty((39, n), dtype=torch.float64, device=dev)
         g = torch.empty((43, n), dtype=torch.float64, device=dev)
-        fn = lambda: tl.tl_dtg_forward_backward(x, gout, y, g, stream=stream)
+        fb_dtype = "f64_ff" if args.variant == "f64_ff" else "f64"
+        fn = lambda: tl.tl_dtg_forward_backward(x, gout, y, g, dtype=fb_dtype, stream=stream)
         units = n
     elif args.only == "fd":
         side = round(n ** (1.0 / 3.0))

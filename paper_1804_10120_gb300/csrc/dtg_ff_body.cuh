@@ -6,12 +6,20 @@
 
 namespace tl {
 
-// The chain on one point's 43 input values (in registers, input-table order), outputs to o.out[s][x].
-// Returns false, having stored nothing but g^ij, when a value falls outside the pair format's range;
-// the caller then evaluates the point in binary64.  kScaled and sd as for chain_f64: the 27 derivative
-// entries are differences still to be multiplied by sd.
+// Intermediates of the float-float chain at one point that the fused forward + adjoint reuses: g^ij in
+// binary64, and 1/2 g^ij, the Eq. 6 bracket, Gamma and beta as pairs.
+struct ChainFFKeep {
+    double ginv[6];
+    ff h[6], T[3][6], gam[3][6], b[3];
+};
+
+// The chain on one point's 43 input values (in registers, input-table order), outputs to o.out[s][x],
+// intermediates to k.  Returns false, having stored nothing but g^ij, when a value falls outside the
+// pair format's range; the caller then evaluates the point in binary64.  kScaled and sd as for
+// chain_f64: the 27 derivative entries are differences still to be multiplied by sd.
 template <class OutTable, bool kScaled = false>
-__device__ __forceinline__ bool chain_ff(const double (&v)[N_IN], const OutTable &o, int64_t x, double sd = 1.0)
+__device__ __forceinline__ bool chain_ff_keep(const double (&v)[N_IN], const OutTable &o, int64_t x, double sd,
+                                              ChainFFKeep &k)
 {
     const double g00 = v[IN_G + 0], g01 = v[IN_G + 1],
                  g02 = v[IN_G + 2], g11 = v[IN_G + 3],
@@ -37,6 +45,7 @@ __device__ __forceinline__ bool chain_ff(const double (&v)[N_IN], const OutTable
     for (int p = 0; p < 6; ++p) {
         const double gi = c[p] * rdet;
         st_stream(o.out[OUT_GINV + p] + x, gi);
+        k.ginv[p] = gi;
         if constexpr (kScaled)
             h[p] = split_ff(gi * half_exact(sd), big);
         else
@@ -59,6 +68,17 @@ __device__ __forceinline__ bool chain_ff(const double (&v)[N_IN], const OutTable
 
     if (big)
         return false;
+#pragma unroll
+    for (int p = 0; p < 6; ++p)
+        k.h[p] = h[p];
+#pragma unroll
+    for (int l = 0; l < 3; ++l)
+#pragma unroll
+        for (int p = 0; p < 6; ++p)
+            k.T[l][p] = T[l][p];
+    k.b[0] = bf0;
+    k.b[1] = bf1;
+    k.b[2] = bf2;
 
     // step 2: Eq. 6 contraction in pairs
     ff gam[3][6];
@@ -68,6 +88,7 @@ __device__ __forceinline__ bool chain_ff(const double (&v)[N_IN], const OutTable
         for (int p = 0; p < 6; ++p) {
             gam[i][p] = dot3_ff(h[sym(i, 0)], T[0][p], h[sym(i, 1)], T[1][p], h[sym(i, 2)], T[2][p]);
             st_stream(o.out[OUT_GAMMA + 6 * i + p] + x, merge_ff(gam[i][p]));
+            k.gam[i][p] = gam[i][p];
         }
 
     // step 3: S_ij = Gamma^k_ij beta_k (symmetric in ij: 6 sums) in pairs, then
@@ -100,6 +121,14 @@ __device__ __forceinline__ bool chain_ff(const double (&v)[N_IN], const OutTable
             st_stream(o.out[OUT_DTG + p] + x, fma(m2a, K, s));
         }
     return true;
+}
+
+// The chain alone (the intermediates are dropped; the compiler removes the copies).
+template <class OutTable, bool kScaled = false>
+__device__ __forceinline__ bool chain_ff(const double (&v)[N_IN], const OutTable &o, int64_t x, double sd = 1.0)
+{
+    ChainFFKeep unused;
+    return chain_ff_keep<OutTable, kScaled>(v, o, x, sd, unused);
 }
 
 }  // namespace tl

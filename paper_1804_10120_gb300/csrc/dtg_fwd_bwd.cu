@@ -13,6 +13,7 @@
 // the second because T^T g^ij = 2 Gamma^T turns -g^ij A g^ij (A = Hbar + Hbar^T, from dH = -H dG H)
 // into -(X + X^T) with X = 2 Tbar Gamma^T (dtg_bwd_body.cuh gives the derivation).
 #include "dtg_bwd_body.cuh"
+#include "dtg_ff_body.cuh"
 #include "tl_kernels.h"
 
 namespace tl {
@@ -119,6 +120,166 @@ __global__ void __launch_bounds__(kFwdBwdThreads, 3) dtg_fwdbwd_f64_kernel(const
     }
 }
 
+// ------------------------------------------------------------------- float-float forward + adjoint
+// The same pass with the float-float arithmetic of TL_F64_FF: the inverse, the Eq. 6 bracket, the
+// folds of the upstream gradients and Eq. 5 in binary64, every contraction -- Eq. 6 and the footnote in
+// the forward, betabar, Gammabar, Tbar, the bracket's scatter and the folded -H A H in the adjoint --
+// in float-float pairs reusing the forward's h, T and Gamma.  A point with a value outside the pair
+// format's range is evaluated again, outputs and gradients, by the binary64 pass.
+template <bool kU, bool kG> __device__ __noinline__ void fwdbwd_point_f64_general(const FwdBwdArgs<double> &a, int64_t x)
+{
+    fwdbwd_point_f64<kU, kG>(a, x);
+}
+
+template <bool kU, bool kG>
+__device__ __forceinline__ void fwdbwd_point_ff(const FwdBwdArgs<double> &a, int64_t x)
+{
+    double v[N_IN];
+#pragma unroll
+    for (int s = 0; s < N_IN; ++s)
+        v[s] = ld_stream(a.in[s] + x);
+    double W[6];
+#pragma unroll
+    for (int p = 0; p < 6; ++p)
+        W[p] = ld_opt(a.gout[OUT_DTG + p], x);
+    asm volatile("" ::: "memory");
+
+    ChainFFKeep c;
+    if (!chain_ff_keep<FwdBwdArgs<double>, false>(v, a, x, 1.0, c)) {
+        fwdbwd_point_f64_general<kU, kG>(a, x);
+        return;
+    }
+    uint32_t big = 0;
+    ff V[3][6];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int p = 0; p < 6; ++p)
+            V[k][p] = split_ff(ld_opt(a.gout[OUT_GAMMA + 6 * k + p], x), big);
+
+    // Eq. 5 and the footnote reversed, in binary64
+    double K[6], S[6];
+#pragma unroll
+    for (int p = 0; p < 6; ++p)
+        K[p] = v[IN_K + p];
+    adj_eq5_footnote<kU, false>(a, x, W, K, v[IN_ALPHA], S);
+    ff Sf[6];
+#pragma unroll
+    for (int p = 0; p < 6; ++p)
+        Sf[p] = split_ff(S[p], big);
+    if (big) {
+        fwdbwd_point_f64_general<kU, kG>(a, x);
+        return;
+    }
+
+    // betabar_k = -sum_p S_p Gamma^k_p
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        ffacc B = acc_prod(Sf[0], c.gam[k][0]);
+#pragma unroll
+        for (int p = 1; p < 6; ++p)
+            acc_add_prod(B, Sf[p], c.gam[k][p]);
+        st_stream(a.gin[IN_BETA + k] + x, neg_exact(merge_ff(acc_result(B))));
+    }
+
+    // Gammabar_kp = V_kp - beta_k S_p
+    ff gb[3][6];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int p = 0; p < 6; ++p) {
+            ffacc A = acc_from(V[k][p]);
+            acc_add_prod(A, ff_neg(c.b[k]), Sf[p]);
+            gb[k][p] = acc_result(A);
+        }
+
+    // Tbar_lp = sum_i h_il Gammabar_ip, scattered through the bracket onto d_k g_ij
+    ff Tb[3][6];
+    ffacc D[18];
+    bool seen[18] = {};
+    auto put = [&](int s, ff t) {   // first contribution assigned (resolved at compile time)
+        if (seen[s])
+            acc_add(D[s], t);
+        else
+            D[s] = acc_from(t);
+        seen[s] = true;
+    };
+#pragma unroll
+    for (int l = 0; l < 3; ++l)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+            for (int k = j; k < 3; ++k) {
+                const int p = sym(j, k);
+                ffacc A = acc_prod(c.h[sym(0, l)], gb[0][p]);
+                acc_add_prod(A, c.h[sym(1, l)], gb[1][p]);
+                acc_add_prod(A, c.h[sym(2, l)], gb[2][p]);
+                const ff t = acc_result(A);
+                Tb[l][p] = t;
+                if (l == j) {
+                    put(3 * sym(j, j) + k, t);
+                } else if (l == k) {
+                    put(3 * sym(k, k) + j, t);
+                } else if (j == k) {
+                    put(3 * sym(j, l) + j, ff_scale(t, 2.0f));
+                    put(3 * sym(j, j) + l, ff_neg(t));
+                } else {
+                    put(3 * sym(j, l) + k, t);
+                    put(3 * sym(l, k) + j, t);
+                    put(3 * sym(j, k) + l, ff_neg(t));
+                }
+            }
+#pragma unroll
+    for (int s = 0; s < 18; ++s)
+        st_stream(a.gin[IN_DG + s] + x, merge_ff(acc_result(D[s])));
+
+    // inverse: gbar = -(X + X^T) folded, X = 2 Tbar Gamma^T (+ the g^ij upstream gradient's -H A_Y H)
+    double F[6];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = i; j < 3; ++j) {
+            ffacc A = acc_prod(Tb[i][0], c.gam[j][0]);
+#pragma unroll
+            for (int p = 1; p < 6; ++p)
+                acc_add_prod(A, Tb[i][p], c.gam[j][p]);
+            if (i != j) {
+#pragma unroll
+                for (int p = 0; p < 6; ++p)
+                    acc_add_prod(A, Tb[j][p], c.gam[i][p]);
+            }
+            F[sym(i, j)] = twice_exact(merge_ff(acc_result(A)));
+        }
+    if (kG) {
+        double Y[6], h[6], P[3][3] = {}, FY[6];
+#pragma unroll
+        for (int p = 0; p < 6; ++p) {
+            Y[p] = ld_opt(a.gout[OUT_GINV + p], x);
+            h[p] = half_exact(c.ginv[p]);
+        }
+        adj_add_hAY<false>(h, Y, P);
+        adj_fold_PH<false>(P, c.ginv, FY);
+#pragma unroll
+        for (int p = 0; p < 6; ++p)
+            F[p] += FY[p];
+    }
+#pragma unroll
+    for (int p = 0; p < 6; ++p)
+        st_stream(a.gin[IN_G + p] + x, neg_exact(F[p]));
+}
+
+// One 256-thread block per SM walking block-sized strides with a barrier per point, as the float-float
+// adjoint does (its body is of the same length).
+template <bool kU, bool kG>
+__global__ void __launch_bounds__(kFwdBwdFfThreads) dtg_fwdbwd_ff_kernel(const FwdBwdArgs<double> a, int64_t n)
+{
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
+        if (base + threadIdx.x < n)
+            fwdbwd_point_ff<kU, kG>(a, base + threadIdx.x);
+        __syncthreads();
+    }
+}
+
 static bool any_present(const double *const *p, int count)
 {
     for (int i = 0; i < count; ++i)
@@ -141,9 +302,26 @@ cudaError_t launch_fwdbwd_f64(const FwdBwdArgs<double> &a, int64_t n, LaunchShap
     return cudaGetLastError();
 }
 
-cudaError_t occupancy_fwdbwd(int *f64)
+cudaError_t launch_fwdbwd_ff(const FwdBwdArgs<double> &a, int64_t n, LaunchShape sh, cudaStream_t s)
 {
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(f64, dtg_fwdbwd_f64_kernel<true, true>, kFwdBwdThreads, 0);
+    const bool hasU = any_present(a.gout + OUT_DBCOV, 9), hasG = any_present(a.gout + OUT_GINV, 6);
+    if (hasU && hasG)
+        dtg_fwdbwd_ff_kernel<true, true><<<sh.grid, sh.threads, 0, s>>>(a, n);
+    else if (hasU)
+        dtg_fwdbwd_ff_kernel<true, false><<<sh.grid, sh.threads, 0, s>>>(a, n);
+    else if (hasG)
+        dtg_fwdbwd_ff_kernel<false, true><<<sh.grid, sh.threads, 0, s>>>(a, n);
+    else
+        dtg_fwdbwd_ff_kernel<false, false><<<sh.grid, sh.threads, 0, s>>>(a, n);
+    return cudaGetLastError();
+}
+
+cudaError_t occupancy_fwdbwd(int *f64, int *ff)
+{
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(f64, dtg_fwdbwd_f64_kernel<true, true>, kFwdBwdThreads, 0);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(ff, dtg_fwdbwd_ff_kernel<false, false>, kFwdBwdFfThreads, 0);
+    return e;
 }
 
 }  // namespace tl

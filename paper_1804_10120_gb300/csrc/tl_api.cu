@@ -65,7 +65,7 @@ tl_status device_info(const DeviceInfo **out)
             if (e == cudaSuccess)
                 e = occupancy_bwd(&d.bwd_f64_blocks, &d.bwd_ff_blocks);
             if (e == cudaSuccess)
-                e = occupancy_fwdbwd(&d.fwdbwd_f64_blocks);
+                e = occupancy_fwdbwd(&d.fwdbwd_f64_blocks, &d.fwdbwd_ff_blocks);
             if (e != cudaSuccess)
                 return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
         }
@@ -405,8 +405,8 @@ tl_status tl_dtg_forward_backward(const tl_dtg_in *in, const tl_dtg_out *out, co
         return fail(TL_ERR_INVALID_ARG, "n = %lld < 0", (long long)n);
     if (!dtype_ok(dtype))
         return fail(TL_ERR_INVALID_ARG, "unknown dtype %d", (int)dtype);
-    if (dtype != TL_F64)
-        return fail(TL_ERR_UNSUPPORTED, "the fused forward + adjoint is provided for TL_F64");
+    if (dtype == TL_F32)
+        return fail(TL_ERR_UNSUPPORTED, "the fused forward + adjoint is provided for TL_F64 and TL_F64_FF");
     const void *const *tabs[4] = {(const void *const *)in, (const void *const *)out, (const void *const *)gout,
                                   (const void *const *)gin};
     const int counts[4] = {N_IN, N_OUT, N_OUT, N_IN};
@@ -428,7 +428,8 @@ tl_status tl_dtg_forward_backward(const tl_dtg_in *in, const tl_dtg_out *out, co
         a.gout[q] = (const double *)((const void *const *)gout)[q];
     }
     const cudaError_t e =
-        launch_fwdbwd_f64(a, n, shape_for(n, kFwdBwdThreads, d->sms, d->fwdbwd_f64_blocks), (cudaStream_t)stream);
+        dtype == TL_F64 ? launch_fwdbwd_f64(a, n, shape_for(n, kFwdBwdThreads, d->sms, d->fwdbwd_f64_blocks), (cudaStream_t)stream)
+                        : launch_fwdbwd_ff(a, n, shape_for(n, kFwdBwdFfThreads, d->sms, d->fwdbwd_ff_blocks), (cudaStream_t)stream);
     return e == cudaSuccess ? TL_OK : cuda_fail(e, "forward + adjoint launch");
 }
 

@@ -19,7 +19,7 @@ struct DeviceInfo {
     bool supported = false;
     int sms = 0;
     int fwd_f64_blocks = 0, fwd_f32_blocks = 0, fwd_ff_blocks = 0, bwd_f64_blocks = 0, bwd_ff_blocks = 0;
-    int fwdbwd_f64_blocks = 0;
+    int fwdbwd_f64_blocks = 0, fwdbwd_ff_blocks = 0;
     char name[256] = {0};
 };
 // Facts about the current device (sm_103 check, SM count, occupancies), queried once per device.

@@ -36,8 +36,10 @@ cudaError_t launch_bwd_f64(const BwdArgs<double> &a, int64_t n, LaunchShape sh, 
 cudaError_t launch_bwd_ff(const BwdArgs<double> &a, int64_t n, LaunchShape sh, cudaStream_t s);
 // Forward and adjoint of one functional in one pass (binary64).
 constexpr int kFwdBwdThreads = 128;
+constexpr int kFwdBwdFfThreads = 256;   // the float-float form (one block per SM)
 cudaError_t launch_fwdbwd_f64(const FwdBwdArgs<double> &a, int64_t n, LaunchShape sh, cudaStream_t s);
-cudaError_t occupancy_fwdbwd(int *f64);
+cudaError_t launch_fwdbwd_ff(const FwdBwdArgs<double> &a, int64_t n, LaunchShape sh, cudaStream_t s);
+cudaError_t occupancy_fwdbwd(int *f64, int *ff);
 
 struct BatchView;
 // Batched forward: one persistent launch over all grids of a plan; `threads` in {128, 256, 512}.

@@ -6,7 +6,7 @@ import pytest
 
 import gridgen
 import oracle
-from tests.parity import TOL_F64, POINTWISE_F64, assert_components, assert_pointwise, IN_NAMES
+from tests.parity import TOL_F64, POINTWISE_F64, POINTWISE_FF, assert_components, assert_pointwise, IN_NAMES
 from tests.test_gpu_backward import upstream
 
 torch = pytest.importorskip("torch")
@@ -94,9 +94,86 @@ def test_fused_empty_and_unsupported():
     x = torch.empty((43, 0), dtype=torch.float64, device=dev())
     y, gin = tl.tl_dtg_forward_backward(x, [None] * 39)
     assert y.shape == (39, 0) and gin.shape == (43, 0)
-    x = torch.from_numpy(gridgen.random_grid(16, 1)).to(dev())
-    with pytest.raises(tl.TLError):
-        tl.tl_dtg_forward_backward(x, [None] * 39, dtype="f64_ff")
+    x = torch.from_numpy(gridgen.random_grid(16, 1)).to(dev(), torch.float32)
+    with pytest.raises(tl.TLError) as e:
+        tl.tl_dtg_forward_backward(x, [None] * 39, dtype="f32")
+    assert e.value.status == 3
+
+
+def run_fused_ff(x, gout):
+    import paper_1804_10120_gb300 as tl
+    xd = torch.from_numpy(x).to(dev())
+    gd = [None if g is None else torch.from_numpy(g).to(dev()) for g in gout]
+    y, gin = tl.tl_dtg_forward_backward(xd, gd, dtype="f64_ff")
+    y_sep = tl.tl_dtg_forward(xd, dtype="f64_ff")
+    torch.cuda.synchronize()
+    return y.cpu().numpy(), gin.cpu().numpy(), y_sep.cpu().numpy()
+
+
+@pytest.mark.parametrize("which", [("gamma", "dtg"), ("ginv", "gamma", "dbcov", "dtg"), ("dtg",), ("gamma",),
+                                   ("dbcov",), ("ginv",), ("ginv", "dtg")])
+def test_fused_ff_matches_ff_forward_and_oracle_adjoint(which):
+    n = 4096
+    x = gridgen.random_grid(n, 3)
+    gout = upstream(n, 3, which)
+    y, gin, y_sep = run_fused_ff(x, gout)
+    assert np.array_equal(y.view(np.uint64), y_sep.view(np.uint64))
+    ref = oracle.backward(x, gout)
+    assert_components(gin, ref, TOL_F64, names=IN_NAMES, what="fused ff %s" % (which,))
+    assert_pointwise(gin, ref, POINTWISE_FF, names=IN_NAMES, what="fused ff %s" % (which,))
+
+
+@pytest.mark.parametrize("n", [1, 129, 255, 65537])
+def test_fused_ff_ragged_and_conformal(n):
+    x = gridgen.random_grid(n, 90 + n)
+    gout = upstream(n, 90 + n, ("ginv", "gamma", "dbcov", "dtg"))
+    y, gin, y_sep = run_fused_ff(x, gout)
+    assert np.array_equal(y.view(np.uint64), y_sep.view(np.uint64))
+    assert_components(gin, oracle.backward(x, gout), TOL_F64, names=IN_NAMES, what="fused ff n=%d" % n)
+    x = gridgen.conformal_grid(12)
+    gout = upstream(x.shape[1], 91, ("ginv", "gamma", "dbcov", "dtg"))
+    y, gin, y_sep = run_fused_ff(x, gout)
+    assert np.array_equal(y.view(np.uint64), y_sep.view(np.uint64))
+    assert_components(gin, oracle.backward(x, gout), TOL_F64, names=IN_NAMES, what="fused ff conformal")
+
+
+def test_fused_ff_binary64_fallback():
+    """Points with an input (beta_0 = 2^70) or an upstream gradient (a Gamma^0_12 upstream gradient of
+    1e200) outside the pair range take the binary64 pass: their outputs and gradients are bit for bit
+    those of the binary64 fused pass, and the points whose inputs are in range keep the float-float
+    outputs.  The oracle gates the points 0-8 and the untouched ones; at the points 8-16 its own sum
+    adds and removes terms of ~1e199 (the two halves of the bracket's d_2 g_12 - d_2 g_21) and drops
+    the O(1) terms between them, so the exact gradient there is the one without cancellation."""
+    n = 2048
+    x = gridgen.random_grid(n, 44)
+    x[31, 0:8] = 2.0 ** 70
+    gout = upstream(n, 45, ("ginv", "gamma", "dbcov", "dtg"))
+    gout[6 + 4][8:16] = 1e200
+    y, gin, y_sep = run_fused_ff(x, gout)
+    ref = oracle.backward(x, gout)
+    for lo, hi in [(0, 8), (16, n)]:
+        assert_components(gin[:, lo:hi], ref[:, lo:hi], TOL_F64, names=IN_NAMES, what="fused ff rows %d-%d" % (lo, hi))
+    assert np.array_equal(y[:, 16:].view(np.uint64), y_sep[:, 16:].view(np.uint64))
+    y64, gin64, _ = run_fused(x, gout)
+    assert np.array_equal(y[:, 0:16].view(np.uint64), y64[:, 0:16].view(np.uint64))
+    assert np.array_equal(gin[:, 0:16].view(np.uint64), gin64[:, 0:16].view(np.uint64))
+
+
+def test_fused_ff_full_size():
+    import paper_1804_10120_gb300 as tl
+    n = 1 << 22
+    x = gridgen.random_grid(n, 3)
+    gout = upstream(n, 3)
+    xd = torch.from_numpy(x).to(dev())
+    gd = [None if g is None else torch.from_numpy(g).to(dev()) for g in gout]
+    y, gin = tl.tl_dtg_forward_backward(xd, gd, dtype="f64_ff")
+    assert torch.equal(y.view(torch.int64), tl.tl_dtg_forward(xd, dtype="f64_ff").view(torch.int64))
+    rng = np.random.default_rng(41)
+    idx = np.unique(np.concatenate([np.arange(300), np.arange(n - 300, n), rng.integers(0, n, 15000)]))
+    ref = oracle.backward(np.ascontiguousarray(x[:, idx]),
+                          [None if g is None else np.ascontiguousarray(g[idx]) for g in gout])
+    gi = gin[:, torch.from_numpy(idx).to(dev())].cpu().numpy()
+    assert_components(gi, ref, TOL_F64, names=IN_NAMES, what="N=2^22 sampled fused ff adjoint")
 
 
 def test_fused_in_cuda_graph_and_with_scattered_tables():
