@@ -368,11 +368,24 @@ def device_facts(dev):
     return sms, mhz
 
 
+def nominal_hbm_gbs(dev):
+    """Nominal HBM bandwidth from the device properties: memory clock x 2 (double data rate) x bus width;
+    None when this PyTorch does not expose them."""
+    import torch
+    p = torch.cuda.get_device_properties(dev)
+    khz, bits = getattr(p, "memory_clock_rate", None), getattr(p, "memory_bus_width", None)
+    if not khz or not bits:
+        return None
+    return (khz * 1e3 * 2 * bits / 8 / 1e9,
+            "device properties: memory clock %d kHz x 2 x %d-bit bus" % (khz, bits))
+
+
 PROBE_OPS = {0: "DFMA", 1: "DADD", 2: "DMUL", 3: "F2F pair (binary64->binary32->binary64)",
-             4: "addition as DFMA by 1.0"}
+             4: "addition as DFMA by 1.0 (immediate)", 5: "DFMA, register operands", 6: "DADD, register operands",
+             7: "DMUL, register operands", 8: "addition as DFMA by 1.0 from constant memory"}
 
 
-def pipe_rates(dev, stream, ops=(0, 1, 2, 3, 4), target_ms=40.0):
+def pipe_rates(dev, stream, ops=tuple(range(9)), target_ms=40.0):
     """Issue rate of each probed operation, operations (op 3: conversion pairs) per second over the whole
     GPU: 8 blocks of 256 threads per SM, 8 independent chains per thread, timed with CUDA events on
     `stream` (the kernel: tl_testing_pipe_rate)."""
@@ -916,6 +929,9 @@ def main():
                 "traffic": traffic, "peak_source": peak_kind + " (MEASURED_PEAKS.json copy bandwidth)",
                 "kernel": KERNEL_NAME[variant], "bytes_per_point": bpp, "avg_launch_ms": avg_launch_s * 1e3}
     sms, max_mhz = device_facts(dev)
+    nominal = nominal_hbm_gbs(dev)
+    if nominal:
+        roofline["nominal_peak"] = {"GB_s": nominal[0], "frac": gbs / nominal[0], "source": nominal[1]}
     fp64 = None
     if variant == "f64":
         # the second ceiling of the binary64 chain: the FP64 pipe (1/64 of the FP32 rate on this part),
@@ -927,9 +943,12 @@ def main():
                 "achieved_gops": FP64_OPS_PER_POINT * n / avg_launch_s / 1e9,
                 "peak_gops": {"DFMA": rates[0] / 1e9, "DADD": rates[1] / 1e9},
                 "floor_ms": floor, "frac": floor / (avg_launch_s * 1e3),
+                "floor_ms_at_dfma_rate": fp64_floor_ms((FWD_FP64_MIX[0] + FWD_FP64_MIX[1], 0), n, rates),
+                "frac_at_dfma_rate": fp64_floor_ms((FWD_FP64_MIX[0] + FWD_FP64_MIX[1], 0), n, rates) / (avg_launch_s * 1e3),
                 "peak_source": "measured: issue rates of tl_testing_pipe_rate on this GPU, same run (8 x 256-thread "
                                "blocks per SM, 8 chains per thread); frac = time the 71 DFMA + 18 DADD per point need "
-                               "at those rates / the kernel's time",
+                               "at those rates / the kernel's time; the additions written as DFMAs (same bits) "
+                               "ran no faster, so the floor with all 89 at the DFMA rate is given beside it",
                 "nominal_peak_gops": 2 * sms * max_mhz / 1e3 if max_mhz else None,
                 "nominal_source": "2 operations/clk/SM x %d SMs x %s MHz (device, nvidia-smi)" % (sms, max_mhz)}
         roofline["second_ceiling"] = {"unit": "FP64 pipe", **fp64}

@@ -54,6 +54,9 @@ TL_API tl_status tl_testing_batched_staged_stall(const tl_batch_plan *plan, tl_s
  * each thread running 8 independent chains of `iters` rounds of one operation:
  *   op 0: DFMA   op 1: DADD   op 2: DMUL   op 3: binary64 -> binary32 -> binary64 conversion pair
  *         (two F2F and one binary32 multiply per round)   op 4: an addition written as an FMA by 1.0
+ *   (an immediate operand); ops 0-4 read their other operands from the parameter bank.
+ *   op 5: DFMA   op 6: DADD   op 7: DMUL, with register operands   op 8: an addition written as an FMA
+ *   whose factor 1.0 comes from constant memory (register addend)
  * so that, timed by the caller, blocks x threads x 8 x iters / time is the issue rate of that
  * operation (op 3: of conversion pairs).  `sink` is a DEVICE array of blocks x threads doubles that
  * is never written for these operands (it only keeps the chains alive).  Enqueued on `stream`.

@@ -3,12 +3,17 @@
 // rounds, so the launch is throughput-bound on that operation's pipe once a few warps share an SM;
 // the host times it and divides the operation count by the time.  The chains' results decide a
 // store that never happens for the operands the host passes, so nothing can be removed.
+// Ops 0-4 take their second and third operands straight from the parameter bank; ops 5-8 take them
+// from registers, as the kernels' operations do (values the compiler cannot see: broadcast by a warp
+// shuffle), and op 8 is an addition written as an FMA whose factor 1.0 is read from constant memory.
 #include "tl_common.cuh"
 #include "../../include/tl_testing.h"
 
 namespace tl {
 
 constexpr int kProbeChains = 8;
+
+static __constant__ double c_probe_unit = 1.0;
 
 template <int OP>
 __global__ void __launch_bounds__(1024) pipe_rate_kernel(double *sink, int64_t iters, double a, double b)
@@ -18,6 +23,7 @@ __global__ void __launch_bounds__(1024) pipe_rate_kernel(double *sink, int64_t i
     for (int k = 0; k < kProbeChains; ++k)
         v[k] = 1.0 + 1e-3 * threadIdx.x + k;
     const float fa = (float)a;
+    const double ra = __shfl_sync(0xffffffffu, a, 0), rb = __shfl_sync(0xffffffffu, b, 0);
     for (int64_t i = 0; i < iters; ++i) {
 #pragma unroll
         for (int k = 0; k < kProbeChains; ++k) {
@@ -32,8 +38,16 @@ __global__ void __launch_bounds__(1024) pipe_rate_kernel(double *sink, int64_t i
                 asm volatile("cvt.rn.f32.f64 %0, %1;" : "=f"(f) : "d"(v[k]));
                 f *= fa;
                 asm volatile("cvt.f64.f32 %0, %1;" : "=d"(v[k]) : "f"(f));
-            } else {
+            } else if (OP == 4) {
                 asm volatile("fma.rn.f64 %0, %1, 0d3FF0000000000000, %2;" : "=d"(v[k]) : "d"(v[k]), "d"(b));   // v*1 + b
+            } else if (OP == 5) {
+                v[k] = fma(v[k], ra, rb);                 // DFMA, register operands
+            } else if (OP == 6) {
+                v[k] = v[k] + rb;                         // DADD, register operands
+            } else if (OP == 7) {
+                v[k] = v[k] * ra;                         // DMUL, register operands
+            } else {
+                v[k] = fma(v[k], c_probe_unit, rb);       // v*1 + b, the 1.0 from constant memory
             }
         }
     }
@@ -50,7 +64,7 @@ __global__ void __launch_bounds__(1024) pipe_rate_kernel(double *sink, int64_t i
 extern "C" TL_API tl_status tl_testing_pipe_rate(int op, int64_t iters, int32_t blocks, int32_t threads, double *sink,
                                                  tl_stream stream)
 {
-    if (op < 0 || op > 4 || iters < 0 || blocks < 1 || threads < 32 || threads > 1024 || threads % 32 || !sink)
+    if (op < 0 || op > 8 || iters < 0 || blocks < 1 || threads < 32 || threads > 1024 || threads % 32 || !sink)
         return TL_ERR_INVALID_ARG;
     const cudaStream_t s = (cudaStream_t)stream;
     // a = 1 keeps every chain finite and exact (b = 0 for the additions); the pipe cost is the same
@@ -59,7 +73,11 @@ extern "C" TL_API tl_status tl_testing_pipe_rate(int op, int64_t iters, int32_t 
     case 1: tl::pipe_rate_kernel<1><<<blocks, threads, 0, s>>>(sink, iters, 1.0, 0.0); break;
     case 2: tl::pipe_rate_kernel<2><<<blocks, threads, 0, s>>>(sink, iters, 1.0, 0.0); break;
     case 3: tl::pipe_rate_kernel<3><<<blocks, threads, 0, s>>>(sink, iters, 1.0, 0.0); break;
-    default: tl::pipe_rate_kernel<4><<<blocks, threads, 0, s>>>(sink, iters, 1.0, 0.0); break;
+    case 4: tl::pipe_rate_kernel<4><<<blocks, threads, 0, s>>>(sink, iters, 1.0, 0.0); break;
+    case 5: tl::pipe_rate_kernel<5><<<blocks, threads, 0, s>>>(sink, iters, 1.0, 0.0); break;
+    case 6: tl::pipe_rate_kernel<6><<<blocks, threads, 0, s>>>(sink, iters, 1.0, 0.0); break;
+    case 7: tl::pipe_rate_kernel<7><<<blocks, threads, 0, s>>>(sink, iters, 1.0, 0.0); break;
+    default: tl::pipe_rate_kernel<8><<<blocks, threads, 0, s>>>(sink, iters, 1.0, 0.0); break;
     }
     return cudaGetLastError() == cudaSuccess ? TL_OK : TL_ERR_CUDA;
 }

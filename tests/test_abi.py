@@ -155,7 +155,7 @@ def test_pipe_rate_probe_argument_checks(L):
     f.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]
     f.restype = ctypes.c_int
     sink = ctypes.c_void_p(1 << 20)
-    assert f(5, 16, 1, 256, sink, None) == 1          # no such operation
+    assert f(9, 16, 1, 256, sink, None) == 1          # no such operation
     assert f(-1, 16, 1, 256, sink, None) == 1
     assert f(0, -1, 1, 256, sink, None) == 1          # negative rounds
     assert f(0, 16, 0, 256, sink, None) == 1          # no blocks

@@ -153,7 +153,7 @@ def test_pipe_rate_probe_runs_and_writes_nothing():
     blocks, threads = 8 * sms, 256
     sink = torch.full((blocks * threads,), float("nan"), dtype=torch.float64, device=dev)
     st = torch.cuda.current_stream(dev)
-    for op in range(5):
+    for op in range(9):
         assert L.tl_testing_pipe_rate(op, 64, blocks, threads, sink.data_ptr(), st.cuda_stream) == 0
     torch.cuda.synchronize()
     assert bool(torch.isnan(sink).all())
