@@ -162,3 +162,24 @@ def test_pipe_rate_probe_argument_checks(L):
     assert f(0, 16, 1, 33, sink, None) == 1           # not whole warps
     assert f(0, 16, 1, 2048, sink, None) == 1         # beyond 1024 threads
     assert f(0, 16, 1, 256, None, None) == 1          # no sink
+
+
+def test_bench_floor_and_nominal_bandwidth(monkeypatch):
+    """The FP64 floor is the operation mix over the measured rates; the nominal HBM figure is memory
+    clock x 2 x bus width from the device properties, and absent when they are not exposed."""
+    import types
+    import torch
+    import bench
+    n = 1 << 24
+    rates = (2.0e9 * 152 * 2.07, 1.68e9 * 152 * 2.07)
+    split = bench.fp64_floor_ms((71, 18), n, rates)
+    all_dfma = bench.fp64_floor_ms((89, 0), n, rates)
+    assert abs(split - (71 / rates[0] + 18 / rates[1]) * n * 1e3) < 1e-12
+    assert all_dfma < split
+    assert abs(all_dfma - 2.37) < 0.02            # 89 x 2^24 / (2 x 152 x 2.07e9) s
+    props = types.SimpleNamespace(memory_clock_rate=3996000, memory_bus_width=8192)
+    monkeypatch.setattr(torch.cuda, "get_device_properties", lambda dev: props)
+    gbs, src = bench.nominal_hbm_gbs(None)
+    assert abs(gbs - 3996e6 * 2 * 1024 / 1e9) < 1e-6 and "8192-bit" in src
+    monkeypatch.setattr(torch.cuda, "get_device_properties", lambda dev: types.SimpleNamespace())
+    assert bench.nominal_hbm_gbs(None) is None
