@@ -20,6 +20,7 @@
 // component the left-hand side reaches is evaluated once, at the first index assignment (row-major)
 // that reaches it -- a symmetric pair is stored once, as in the paper's lookup table.
 // Component storage order of a tensor: its stored index tuples in row-major order.
+#include "../../include/tl_testing.h"
 #include <dlfcn.h>
 
 #include <functional>
@@ -28,6 +29,7 @@
 #include <cctype>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -541,6 +543,8 @@ struct GenState {
     std::set<int> used_inputs;
     std::vector<std::set<int>> defined;
     std::map<std::string, std::string> recip;   // divisor code -> variable holding its reciprocal
+    std::map<std::string, std::string> scaled;  // "factor|k" -> variable holding factor * 2^k
+    int hoisted = 0;                            // names of hoisted values are never reused
     std::ostringstream *body = nullptr;
 };
 
@@ -565,7 +569,7 @@ bool product_factors(const Program &P, const Expr &e, Binding &bind, GenState &G
         const std::string den = gen(P, *e.b, bind, G);
         auto it = G.recip.find(den);
         if (it == G.recip.end()) {
-            const std::string name = "r_" + std::to_string(G.recip.size());
+            const std::string name = "r_" + std::to_string(G.hoisted++);
             *G.body << "    const double " << name << " = tl_rcp(" << den << ");\n";
             it = G.recip.emplace(den, name).first;
         }
@@ -633,8 +637,10 @@ void addends(const Program &P, const Expr &e, Binding &bind, GenState &G, int si
 
 // A signed sum.  Addends that are the same code with opposite signs cancel (e.g. the two bracket terms
 // of Eq. 6 that name one stored element) and repeats merge into a coefficient.  The remaining plain
-// addends are summed left to right; then every product is fused into the running sum with an FMA, so
-// a sum of products costs one stand-alone product (tl_mul, integer pipes) and FMAs.
+// addends are summed left to right, then those with a coefficient other than +-1 (a power of two fused
+// into an FMA with the running sum: RN(s + 2^k a) in one operation, 2^k a being exact), then every
+// product is fused into the running sum with an FMA, so a sum of products costs one stand-alone
+// product (tl_mul, integer pipes) and FMAs.
 std::string sum_code(const std::vector<Term> &terms)
 {
     std::vector<Term> kept;
@@ -650,19 +656,24 @@ std::string sum_code(const std::vector<Term> &terms)
             kept.push_back(t);
     }
     std::string s;
-    for (int pass = 0; pass < 2; ++pass)
+    for (int pass = 0; pass < 3; ++pass)
         for (auto &k : kept) {
             if (k.sign == 0)
                 continue;
             const int mag = k.sign < 0 ? -k.sign : k.sign;
             const bool fuse = k.prod && mag == 1;
-            if (fuse != (pass == 1))
+            const bool pow2 = (mag & (mag - 1)) == 0 && mag <= 256;
+            const int want = fuse ? 2 : (mag > 1 && pow2 ? 1 : 0);
+            if (want != pass)
                 continue;
             if (fuse && !s.empty()) {
                 s = "fma(" + (k.sign < 0 ? "(-" + k.x + ")" : k.x) + ", " + k.y + ", " + s + ")";
                 continue;
             }
-            const bool pow2 = (mag & (mag - 1)) == 0 && mag <= 256;
+            if (pass == 1 && !s.empty()) {
+                s = "fma(" + std::string(k.sign < 0 ? "-" : "") + std::to_string(mag) + ".0, " + k.code + ", " + s + ")";
+                continue;
+            }
             int lg = 0;
             while ((1 << lg) < mag)
                 ++lg;
@@ -721,7 +732,34 @@ std::string gen(const Program &P, const Expr &e, Binding &bind, GenState &G)
                 int k = 0;
                 const double m = frexp(num.num, &k);   // the side that product_factors found to be +-2^k
                 if (m == 0.5 && k - 1 >= -8 && k - 1 <= 8 && k - 1 != 0) {
-                    const std::string scaled = "tl_pow2(" + gen(P, other, bind, G) + ", " + std::to_string(k - 1) + ")";
+                    const std::string lg = std::to_string(k - 1);
+                    // +-2^k times a sum whose addends are all genuine products: the scaling moves onto
+                    // the first factor of each product (2^k a b = (2^k a) b exactly, away from the
+                    // extremes of the range), where identical scaled factors are formed once, instead of
+                    // onto every sum (the 1/2 of Eq. 6 on the 6 stored g^il rather than the 18 Gamma)
+                    if (other.kind == Expr::ADD || other.kind == Expr::SUB || other.kind == Expr::NEG ||
+                        other.kind == Expr::SUM) {
+                        std::vector<Term> terms;
+                        addends(P, other, bind, G, neg ? -1 : 1, terms);
+                        bool all_prod = !terms.empty();
+                        for (auto &t : terms)
+                            all_prod = all_prod && t.prod;
+                        if (all_prod) {
+                            for (auto &t : terms) {
+                                auto it = G.scaled.find(t.x + "|" + lg);
+                                if (it == G.scaled.end()) {
+                                    const std::string name = "s_" + std::to_string(G.hoisted++);
+                                    *G.body << "    const double " << name << " = tl_pow2(" << t.x << ", " << lg << ");\n";
+                                    it = G.scaled.emplace(t.x + "|" + lg, name).first;
+                                }
+                                t.x = it->second;
+                                t.code = "tl_mul(" + t.x + ", " + t.y + ")";
+                            }
+                            return sum_code(terms);
+                        }
+                        return "tl_pow2(" + sum_code(terms) + ", " + lg + ")";
+                    }
+                    const std::string scaled = "tl_pow2(" + gen(P, other, bind, G) + ", " + lg + ")";
                     return neg ? "(-" + scaled + ")" : scaled;
                 }
             }
@@ -812,10 +850,26 @@ void generate(Program &P)
 
     GenState G;
     G.defined.resize(P.tensors.size());
-    std::ostringstream body;
-    G.body = &body;
+    // Each input is loaded just before the first statement that reads it (prefetched into L1 at the top
+    // of the point when that statement is not the first to read inputs), and each output is stored
+    // right after the last statement that assigns it: the registers an input or an output occupies are
+    // held only while it is in use, as in the hand-written kernels.
+    std::vector<int> last_def(P.tensors.size(), -1);
+    for (size_t k = 0; k < P.stmts.size(); ++k)
+        last_def[P.stmts[k].tensor] = (int)k;
+    std::vector<std::pair<int, int>> in_of(P.n_in > 0 ? (size_t)P.n_in : 0);   // table position -> (tensor, slot)
+    for (auto &t : P.tensors)
+        if (t.kind == 0)
+            for (size_t slot = 0; slot < t.stored.size(); ++slot)
+                in_of[(size_t)(t.table_base + (int)slot)] = {(int)(&t - &P.tensors[0]), (int)slot};
+    std::ostringstream body, prefetch;
+    bool loaded_any = false;
     for (auto &st : P.stmts) {
         const Tensor &t = P.tensors[st.tensor];
+        const int si = (int)(&st - &P.stmts[0]);
+        std::ostringstream sb;
+        G.body = &sb;
+        const std::set<int> read_before = G.used_inputs;
         std::map<char, int> free_rhs;
         free_letters(P, *st.rhs, free_rhs, std::set<char>());
         std::set<char> lhs_letters;
@@ -858,8 +912,7 @@ void generate(Program &P)
             const int slot = t.slot_of.at(tup);
             if (std::find(done_slots.begin(), done_slots.end(), slot) == done_slots.end()) {
                 std::string rhs = gen(P, *st.rhs, bind, G);
-                body << "    const double " << value_name(P, st.tensor, slot) << "_s" << &st - &P.stmts[0] << " = " << rhs
-                     << ";\n";
+                sb << "    const double " << value_name(P, st.tensor, slot) << "_s" << si << " = " << rhs << ";\n";
                 done_slots.push_back(slot);
             }
             int r = (int)letters.size() - 1;
@@ -868,13 +921,44 @@ void generate(Program &P)
             if (r < 0)
                 break;
         }
-        // publish this statement's values under the tensor's component names
+        // the inputs this statement reads first, loaded here; then its code
+        std::vector<int> fresh;
+        for (int q : G.used_inputs)
+            if (!read_before.count(q))
+                fresh.push_back(q);
+        if (!fresh.empty()) {
+            if (loaded_any)
+                body << "    asm volatile(\"\" ::: \"memory\");   // not hoisted above the statements before\n";
+            for (int q : fresh) {
+                const auto ts = in_of[(size_t)q];
+                body << "    const double " << value_name(P, ts.first, ts.second) << " = __ldcs(a.in[" << q << "] + x);\n";
+                if (loaded_any)
+                    prefetch << "    asm volatile(\"prefetch.global.L1 [%0];\" :: \"l\"(a.in[" << q << "] + x));\n";
+            }
+            if (!loaded_any)
+                body << "    asm volatile(\"\" ::: \"memory\");   // issued before any arithmetic\n";
+            loaded_any = true;
+        }
+        body << sb.str();
+        // publish this statement's values under the tensor's component names; a component assigned a
+        // second time invalidates the hoisted reciprocals and scaled factors (they may name it)
+        for (int slot : done_slots)
+            if (G.defined[st.tensor].count(slot)) {
+                G.recip.clear();
+                G.scaled.clear();
+            }
         for (int slot : done_slots) {
             body << "    " << (G.defined[st.tensor].count(slot) ? "" : "double ") << value_name(P, st.tensor, slot)
                  << " = " << value_name(P, st.tensor, slot) << "_s" << &st - &P.stmts[0] << ";\n";
             G.defined[st.tensor].insert(slot);
         }
+        if (t.kind == 1 && last_def[st.tensor] == si)
+            for (size_t slot = 0; slot < t.stored.size(); ++slot)
+                if (G.defined[st.tensor].count((int)slot))
+                    body << "    __stcs(a.out[" << t.table_base + (int)slot << "] + x, "
+                         << value_name(P, st.tensor, (int)slot) << ");\n";
     }
+    G.body = nullptr;
     for (auto &t : P.tensors)
         if (t.kind == 1)
             for (size_t slot = 0; slot < t.stored.size(); ++slot)
@@ -897,22 +981,12 @@ void generate(Program &P)
         << "  return tl_pow2_slow(x, k);\n}\n"
         << kMulSource
         << "struct TlJitArgs { const double *in[" << std::max(P.n_in, 1) << "]; double *out[" << P.n_out << "]; };\n"
-        << "extern \"C\" __global__ void __launch_bounds__(256, 2) tl_jit_kernel(const TlJitArgs a, long long n)\n{\n"
+        << "#ifndef TL_JIT_MIN_BLOCKS\n#define TL_JIT_MIN_BLOCKS 2\n#endif\n"
+        << "extern \"C\" __global__ void __launch_bounds__(256, TL_JIT_MIN_BLOCKS) tl_jit_kernel(const TlJitArgs a, "
+           "long long n)\n{\n"
         << "  for (long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x; x < n;\n"
         << "       x += (long long)gridDim.x * blockDim.x) {\n";
-    for (auto &t : P.tensors)
-        if (t.kind == 0)
-            for (size_t slot = 0; slot < t.stored.size(); ++slot)
-                if (G.used_inputs.count(t.table_base + (int)slot))
-                    src << "    const double " << value_name(P, &t - &P.tensors[0], (int)slot) << " = __ldcs(a.in["
-                        << t.table_base + slot << "] + x);\n";
-    src << "    asm volatile(\"\" ::: \"memory\");\n" << body.str();
-    for (auto &t : P.tensors)
-        if (t.kind == 1)
-            for (size_t slot = 0; slot < t.stored.size(); ++slot)
-                src << "    __stcs(a.out[" << t.table_base + slot << "] + x, "
-                    << value_name(P, &t - &P.tensors[0], (int)slot) << ");\n";
-    src << "  }\n}\n";
+    src << prefetch.str() << body.str() << "  }\n}\n";
     P.source = src.str();
     P.reads.assign((size_t)P.n_in, 0);
     for (int q : G.used_inputs)
@@ -965,30 +1039,64 @@ bool load_nvrtc(std::string &why)
     return g_nvrtc.ok;
 }
 
-// Compiled images by generated source: programs that generate the same source compile once per process.
-std::map<std::string, std::vector<char>> g_cubin_cache;
+// Compiled images by generated source (with the blocks per SM they were compiled for): programs that
+// generate the same source compile once per process.
+std::map<std::string, std::pair<std::vector<char>, int>> g_cubin_cache;
 std::mutex g_cubin_mu;
 
-bool nvrtc_compile_uncached(const std::string &src, std::vector<char> &cubin, std::string &log);
+bool nvrtc_compile_uncached(const std::string &src, std::vector<char> &cubin, std::string &log, int &min_blocks);
 
-bool nvrtc_compile(const std::string &src, std::vector<char> &cubin, std::string &log)
+bool nvrtc_compile(const std::string &src, std::vector<char> &cubin, std::string &log, int &min_blocks)
 {
     {
         std::lock_guard<std::mutex> lk(g_cubin_mu);
         auto it = g_cubin_cache.find(src);
         if (it != g_cubin_cache.end()) {
-            cubin = it->second;
+            cubin = it->second.first;
+            min_blocks = it->second.second;
             return true;
         }
     }
-    if (!nvrtc_compile_uncached(src, cubin, log))
+    if (!nvrtc_compile_uncached(src, cubin, log, min_blocks))
         return false;
     std::lock_guard<std::mutex> lk(g_cubin_mu);
-    g_cubin_cache.emplace(src, cubin);
+    g_cubin_cache.emplace(src, std::make_pair(cubin, min_blocks));
     return true;
 }
 
-bool nvrtc_compile_uncached(const std::string &src, std::vector<char> &cubin, std::string &log)
+// Bytes of spill stores ptxas reports for tl_jit_kernel in a compile log (-1 when the log has none).
+long spill_stores(const std::string &log)
+{
+    const size_t k = log.find("Function properties for tl_jit_kernel");
+    if (k == std::string::npos)
+        return -1;
+    const size_t s = log.find("bytes spill stores", k);
+    if (s == std::string::npos)
+        return -1;
+    size_t b = log.rfind(',', s);
+    b = (b == std::string::npos || b < k) ? log.find('.', k) : b;
+    return b == std::string::npos ? -1 : strtol(log.c_str() + b + 1, nullptr, 10);
+}
+
+bool nvrtc_compile_once(const std::string &src, int min_blocks, std::vector<char> &cubin, std::string &log);
+
+// Three 256-thread blocks per SM (at most 85 registers) unless that spills more than 128 bytes per
+// thread, then two (at most 128): a long chain such as Eq. 6 fits in 80 registers at three blocks
+// and runs faster with the extra warps (3.03 -> 2.98 ms for the chain at N = 2^24), while the large
+// contractions keep their registers.
+bool nvrtc_compile_uncached(const std::string &src, std::vector<char> &cubin, std::string &log, int &min_blocks)
+{
+    min_blocks = 3;
+    if (!nvrtc_compile_once(src, min_blocks, cubin, log))
+        return false;
+    const long spills = spill_stores(log);
+    if (spills >= 0 && spills <= 128)
+        return true;
+    min_blocks = 2;
+    return nvrtc_compile_once(src, min_blocks, cubin, log);
+}
+
+bool nvrtc_compile_once(const std::string &src, int min_blocks, std::vector<char> &cubin, std::string &log)
 {
     if (!load_nvrtc(log))
         return false;
@@ -997,8 +1105,10 @@ bool nvrtc_compile_uncached(const std::string &src, std::vector<char> &cubin, st
         log = "nvrtcCreateProgram failed";
         return false;
     }
-    const char *opts[] = {"--gpu-architecture=sm_103a", "-std=c++17", "-default-device"};
-    const int rc = g_nvrtc.compile(prog, 3, opts);
+    const std::string blocks = "-DTL_JIT_MIN_BLOCKS=" + std::to_string(min_blocks);
+    const char *opts[] = {"--gpu-architecture=sm_103a", "-std=c++17", "-default-device", "--ptxas-options=-v",
+                          blocks.c_str()};
+    const int rc = g_nvrtc.compile(prog, 5, opts);
     size_t ls = 0;
     g_nvrtc.log_size(prog, &ls);
     log.assign(ls, '\0');
@@ -1026,6 +1136,7 @@ struct tl_jit_kernel {
     uint64_t magic = 0;
     tl::jit::Program prog;
     std::vector<char> cubin;
+    int min_blocks = 0;                         // the launch bound it was compiled for (blocks per SM)
     std::mutex mu;
     cudaLibrary_t lib[tl::kMaxDevices] = {};
     cudaKernel_t kern[tl::kMaxDevices] = {};
@@ -1056,7 +1167,7 @@ tl_status tl_jit_compile(const char *program, tl_jit_kernel **out, char *log, si
     } catch (const jit::Error &e) {
         why = e.msg;
     }
-    if (ok && !jit::nvrtc_compile(k->prog.source, k->cubin, why)) {
+    if (ok && !jit::nvrtc_compile(k->prog.source, k->cubin, why, k->min_blocks)) {
         ok = false;
         why = "NVRTC: " + why;
     }
@@ -1160,3 +1271,11 @@ void tl_jit_destroy(tl_jit_kernel *k)
 }
 
 }  // extern "C"
+
+extern "C" TL_API tl_status tl_testing_jit_min_blocks(const tl_jit_kernel *k, int32_t *blocks)
+{
+    if (!k || k->magic != kJitMagic || !blocks)
+        return TL_ERR_INVALID_ARG;
+    *blocks = k->min_blocks;
+    return TL_OK;
+}

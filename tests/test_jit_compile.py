@@ -94,3 +94,33 @@ def test_component_split_of_fixed_and_offset_indices():
     assert "Sum(c, E(3,c)*F(c,0))" in pieces[("D", (0, 2))]
     assert "E(0,0)" in pieces[("D", (0, 3))]
     assert len(pieces) == 10
+
+
+def test_launch_bound_follows_the_spill_report(tl):
+    """A program whose kernel fits three 256-thread blocks per SM without spilling more than 128 bytes is
+    built for three (the chain); one that would spill more is rebuilt for two (a rank-4 contraction
+    holding its 81 results); and the generated kernel stores each output right after the statement
+    that finishes it and loads each input just before its first use."""
+    import ctypes
+    from paper_1804_10120_gb300.programs import CHAIN, CHAIN_SYM
+    L = tl.lib()
+    L.tl_testing_jit_min_blocks.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32)]
+    L.tl_testing_jit_min_blocks.restype = ctypes.c_int
+
+    def blocks(text):
+        k = tl.JitKernel(text)
+        b = ctypes.c_int32()
+        assert L.tl_testing_jit_min_blocks(k._h, ctypes.byref(b)) == 0
+        src = k.source
+        k.close()
+        return b.value, src
+
+    b_chain, src = blocks(CHAIN_SYM)
+    assert b_chain == 3 and blocks(CHAIN)[0] == 3
+    assert blocks("in B(3,3); in E(3,3,3,3); out A(3,3,3,3); A(i,j,k,l) = Sum(m, B(i,m)*E(m,j,k,l));")[0] == 2
+    body = src[src.index("tl_jit_kernel("):]
+    # Gamma (out[6..23]) is stored before beta (in[31]) is loaded; K (in[24]) is loaded after dbcov is stored
+    assert body.index("a.out[6] + x") < body.index("__ldcs(a.in[31] + x)") < body.index("a.out[24] + x")
+    assert body.index("a.out[32] + x") < body.index("__ldcs(a.in[24] + x)")
+    assert body.index('"l"(a.in[24] + x)') < body.index("__ldcs(a.in[0] + x)")   # prefetched at the top
+    assert L.tl_testing_jit_min_blocks(None, ctypes.byref(ctypes.c_int32())) == 1
