@@ -64,8 +64,10 @@ TL_API tl_status tl_testing_batched_staged_stall(const tl_batch_plan *plan, tl_s
 TL_API tl_status tl_testing_pipe_rate(int op, int64_t iters, int32_t blocks, int32_t threads, double *sink,
                                       tl_stream stream);
 /*
- * tl_testing_jit_min_blocks: the blocks per SM of 256 threads that a compiled program's kernel was built
- * for (its launch bound): 3 unless that spilled more than 128 bytes per thread, then 2.  Host only.
+ * tl_testing_jit_min_blocks: the blocks per SM of 256 threads that a compiled program's kernel is built
+ * for (its launch bound): 3 unless that spills more than 128 bytes per thread, then 2.  Decided from the
+ * ptxas report in the compile log when it has one, and checked again against the loaded kernel's local
+ * memory at its first launch on a device.  Host only.
  */
 TL_API tl_status tl_testing_jit_min_blocks(const tl_jit_kernel *k, int32_t *blocks);
 

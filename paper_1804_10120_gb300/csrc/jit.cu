@@ -1064,6 +1064,12 @@ bool nvrtc_compile(const std::string &src, std::vector<char> &cubin, std::string
     return true;
 }
 
+void remember_cubin(const std::string &src, const std::vector<char> &cubin, int min_blocks)
+{
+    std::lock_guard<std::mutex> lk(g_cubin_mu);
+    g_cubin_cache[src] = std::make_pair(cubin, min_blocks);
+}
+
 // Bytes of spill stores ptxas reports for tl_jit_kernel in a compile log (-1 when the log has none).
 long spill_stores(const std::string &log)
 {
@@ -1083,14 +1089,15 @@ bool nvrtc_compile_once(const std::string &src, int min_blocks, std::vector<char
 // Three 256-thread blocks per SM (at most 85 registers) unless that spills more than 128 bytes per
 // thread, then two (at most 128): a long chain such as Eq. 6 fits in 80 registers at three blocks
 // and runs faster with the extra warps (3.03 -> 2.98 ms for the chain at N = 2^24), while the large
-// contractions keep their registers.
+// contractions keep their registers.  The ptxas report in the compile log decides here when it is
+// there; the first load on a device checks the kernel's local memory as well.
 bool nvrtc_compile_uncached(const std::string &src, std::vector<char> &cubin, std::string &log, int &min_blocks)
 {
     min_blocks = 3;
     if (!nvrtc_compile_once(src, min_blocks, cubin, log))
         return false;
     const long spills = spill_stores(log);
-    if (spills >= 0 && spills <= 128)
+    if (spills <= 128)   // no report (-1): the first load on a device decides
         return true;
     min_blocks = 2;
     return nvrtc_compile_once(src, min_blocks, cubin, log);
@@ -1240,6 +1247,31 @@ tl_status tl_jit_launch(tl_jit_kernel *k, const double *const *in, double *const
                 return cuda_fail(e, "cudaLibraryLoadData");
             if ((e = cudaLibraryGetKernel(&k->kern[dev], k->lib[dev], "tl_jit_kernel")) != cudaSuccess)
                 return cuda_fail(e, "cudaLibraryGetKernel");
+            if (k->min_blocks == 3) {
+                // The loaded kernel's local memory decides (the compile log carries no ptxas report
+                // under some tools, e.g. a profiler): more than 128 bytes per thread at three blocks
+                // per SM, and it is rebuilt for two.
+                cudaFuncAttributes fa;
+                if ((e = cudaFuncGetAttributes(&fa, (const void *)k->kern[dev])) != cudaSuccess)
+                    return cuda_fail(e, "cudaFuncGetAttributes");
+                if (fa.localSizeBytes > 128) {
+                    std::vector<char> cubin;
+                    std::string why;
+                    if (!jit::nvrtc_compile_once(k->prog.source, 2, cubin, why))
+                        return fail(TL_ERR_INVALID_ARG, "NVRTC: %s", why.c_str());
+                    cudaLibraryUnload(k->lib[dev]);
+                    k->lib[dev] = nullptr;
+                    k->kern[dev] = nullptr;
+                    k->cubin.swap(cubin);
+                    k->min_blocks = 2;
+                    jit::remember_cubin(k->prog.source, k->cubin, 2);
+                    if ((e = cudaLibraryLoadData(&k->lib[dev], k->cubin.data(), nullptr, nullptr, 0, nullptr, nullptr,
+                                                 0)) != cudaSuccess)
+                        return cuda_fail(e, "cudaLibraryLoadData");
+                    if ((e = cudaLibraryGetKernel(&k->kern[dev], k->lib[dev], "tl_jit_kernel")) != cudaSuccess)
+                        return cuda_fail(e, "cudaLibraryGetKernel");
+                }
+            }
             if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k->blocks[dev], (const void *)k->kern[dev], 256, 0)) !=
                 cudaSuccess)
                 return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");

@@ -148,3 +148,27 @@ def test_generated_chain_with_symmetric_footnote_sum():
     assert_components(y_gen.cpu().numpy()[:, idx], oracle.forward(np.ascontiguousarray(x[:, idx])), TOL_F64,
                       what="symmetric-sum chain")
     k.close()
+
+
+def test_launch_bound_kept_after_loading():
+    """The first launch checks the loaded kernel's local memory: the chain keeps three blocks per SM
+    (80 registers, a few dozen bytes spilled), the rank-4 contraction stays at two, and both still
+    match the reference interpreter."""
+    import ctypes
+    import paper_1804_10120_gb300 as tl
+    from paper_1804_10120_gb300.programs import CHAIN_SYM
+    from oracle.tensor_expr import Program
+    L = tl.lib()
+    L.tl_testing_jit_min_blocks.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32)]
+    rank4 = "in B(3,3); in E(3,3,3,3); out A(3,3,3,3); A(i,j,k,l) = Sum(m, B(i,m)*E(m,j,k,l));"
+    for text, want in ((CHAIN_SYM, 3), (rank4, 2)):
+        k = tl.JitKernel(text)
+        n = 1000
+        x = gridgen.random_grid(n, 7) if text is CHAIN_SYM else gridgen.normal_fields(k.n_in, n, 7, 6000)
+        y = k.launch(torch.from_numpy(x).to(dev()))
+        torch.cuda.synchronize()
+        b = ctypes.c_int32()
+        assert L.tl_testing_jit_min_blocks(k._h, ctypes.byref(b)) == 0 and b.value == want
+        ref = Program(text).run(x)
+        assert component_errors(y.cpu().numpy(), ref).max() <= TOL_F64
+        k.close()
