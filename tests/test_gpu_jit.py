@@ -172,3 +172,26 @@ def test_launch_bound_kept_after_loading():
         ref = Program(text).run(x)
         assert component_errors(y.cpu().numpy(), ref).max() <= TOL_F64
         k.close()
+
+
+def test_generated_chain_full_size():
+    """The generated chain at the benchmark's size and launch (N = 2^24, seed 1, three blocks per SM):
+    every point within the binary64 gate of the hand kernel, and a sample of points against the
+    oracle."""
+    import paper_1804_10120_gb300 as tl
+    from paper_1804_10120_gb300.programs import CHAIN
+    n = 1 << 24
+    x = gridgen.random_grid(n, 1)
+    xd = torch.from_numpy(x).to(dev())
+    k = tl.JitKernel(CHAIN)
+    y_gen = k.launch(xd)
+    y_hand = tl.tl_dtg_forward(xd)
+    torch.cuda.synchronize()
+    err = ((y_gen - y_hand).abs().amax(dim=1) / y_hand.abs().amax(dim=1)).max().item()
+    assert err <= TOL_F64, err
+    rng = np.random.default_rng(13)
+    idx = np.unique(np.concatenate([np.arange(256), np.arange(n - 256, n), rng.integers(0, n, 20000)]))
+    yg = y_gen[:, torch.from_numpy(idx).to(dev())].cpu().numpy()
+    assert_components(yg, oracle.forward(np.ascontiguousarray(x[:, idx])), TOL_F64, what="generated chain, N=2^24")
+    del y_gen, y_hand, xd
+    k.close()
