@@ -99,12 +99,13 @@ TL_API tl_status tl_dtg_backward(const tl_dtg_in *in, const tl_dtg_gout *gout, c
 /*
  * Forward and adjoint in one pass, for a functional whose upstream gradients are known before the forward
  * runs (L = sum gout * out with gout given up front, e.g. a loss linear in the outputs): writes the 39
- * outputs exactly as tl_dtg_forward does (bit for bit) and the 43 input gradients as tl_dtg_backward
- * does (same definition; rounding may differ in the last bits), reading every input once.  g^ij, the
- * Eq. 6 bracket and Gamma are formed once and serve both.  TL_F64: binary64 throughout.  TL_F64_FF:
- * the arithmetic of TL_F64_FF (contractions in float-float pairs, the rest in binary64); a point whose
- * inputs or upstream gradients fall outside the pair format's range is evaluated, outputs and
- * gradients, in binary64 (its outputs are then the binary64 forward's).  TL_F32: TL_ERR_UNSUPPORTED.
+ * outputs exactly as tl_dtg_forward with the same dtype does (bit for bit) and the 43 input gradients
+ * as tl_dtg_backward does (same definition; rounding may differ in the last bits), reading every input
+ * once.  g^ij, the Eq. 6 bracket and Gamma are formed once and serve both.  TL_F64: binary64
+ * throughout.  TL_F64_FF: the arithmetic of TL_F64_FF (contractions in float-float pairs, the rest in
+ * binary64); a point whose inputs fall outside the pair format's range is evaluated in binary64, as the
+ * float-float forward does, and one whose upstream gradients do gets its gradients from the binary64
+ * adjoint (bit for bit those of tl_dtg_backward with TL_F64).  TL_F32: TL_ERR_UNSUPPORTED.
  * Same rules as tl_dtg_forward and tl_dtg_backward; out and gin must not overlap each other, in or gout.
  */
 TL_API tl_status tl_dtg_forward_backward(const tl_dtg_in *in, const tl_dtg_out *out, const tl_dtg_gout *gout,

@@ -149,4 +149,105 @@ __device__ __forceinline__ void adj_fold_PH(const double (&P)[3][3], const doubl
         }
 }
 
+// The binary64 adjoint at one point (a: any argument block with `in`, `gout` and `gin` tables).  kU:
+// upstream gradient of nabla beta present; kG: upstream gradient of g^ij present.  kIntMul: the 59
+// products not fused into an FMA run on the integer pipes (mul_int, the same bits as the FP64 multiply).
+template <bool kU, bool kG, bool kIntMul = true, class Args = BwdArgs<double>>
+__device__ __forceinline__ void bwd_point_f64(const Args &a, int64_t x)
+{
+    // ---- recompute: inverse metric and bracket
+    const double g00 = ld_stream(a.in[IN_G + 0] + x), g01 = ld_stream(a.in[IN_G + 1] + x),
+                 g02 = ld_stream(a.in[IN_G + 2] + x), g11 = ld_stream(a.in[IN_G + 3] + x),
+                 g12 = ld_stream(a.in[IN_G + 4] + x), g22 = ld_stream(a.in[IN_G + 5] + x);
+    double dg[18];
+#pragma unroll
+    for (int s = 0; s < 18; ++s)
+        dg[s] = ld_stream(a.in[IN_DG + s] + x);
+    double H[6], h[6];
+    {
+        double c[6];
+        c[0] = fma(g11, g22, -mul64<kIntMul>(g12, g12));
+        c[1] = fma(g02, g12, -mul64<kIntMul>(g01, g22));
+        c[2] = fma(g01, g12, -mul64<kIntMul>(g02, g11));
+        c[3] = fma(g00, g22, -mul64<kIntMul>(g02, g02));
+        c[4] = fma(g01, g02, -mul64<kIntMul>(g00, g12));
+        c[5] = fma(g00, g11, -mul64<kIntMul>(g01, g01));
+        const double det = fma(g00, c[0], fma(g01, c[1], mul64<kIntMul>(g02, c[2])));
+        const double rdet = rcp_f64(det);
+#pragma unroll
+        for (int p = 0; p < 6; ++p) {
+            H[p] = mul64<kIntMul>(c[p], rdet);
+            h[p] = half_exact(H[p]);
+        }
+    }
+    double T[3][6];
+    christoffel_bracket<double>(dg, T);
+
+    // ---- Eq. 5 and the footnote, reversed
+    double W[6], K[6], S[6];
+#pragma unroll
+    for (int p = 0; p < 6; ++p) {
+        W[p] = ld_opt(a.gout[OUT_DTG + p], x);
+        K[p] = ld_stream(a.in[IN_K + p] + x);
+    }
+    adj_eq5_footnote<kU, kIntMul>(a, x, W, K, ld_stream(a.in[IN_ALPHA] + x), S);
+
+    // betabar_k = -sum_p S_p Gamma^k_p = -sum_l h_kl u_l with u_l = sum_p S_p T_lp: Gamma itself is
+    // never needed by the adjoint
+    double u[3], beta[3];
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+        double s = mul64<kIntMul>(S[0], T[l][0]);
+#pragma unroll
+        for (int p = 1; p < 6; ++p)
+            s = fma(S[p], T[l][p], s);
+        u[l] = s;
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        beta[k] = ld_stream(a.in[IN_BETA + k] + x);
+        // the sign on the integer pipe: the compiler negates a binary64 result with an FP64 addition
+        st_stream(a.gin[IN_BETA + k] + x,
+                  neg_exact(fma(h[sym(k, 2)], u[2], fma(h[sym(k, 1)], u[1], mul64<kIntMul>(h[sym(k, 0)], u[0])))));
+    }
+
+    // ---- Gamma: Gammabar = V - beta_k S_p
+    double gbar[3][6];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int p = 0; p < 6; ++p)
+            gbar[k][p] = fma(-beta[k], S[p], ld_opt(a.gout[OUT_GAMMA + 6 * k + p], x));
+
+    // ---- Eq. 6: Tbar, scattered onto d_k g_ij
+    double Tb[3][6];
+    adj_tbar<kIntMul>(h, gbar, Tb);
+    adj_bracket_store(a, x, Tb);
+
+    // ---- inverse: P = Tbar T^T (= H Hbar), plus h A_Y; gbar = -fold(P H)
+    double P[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int l = 0; l < 3; ++l) {
+            double s = mul64<kIntMul>(Tb[i][0], T[l][0]);
+#pragma unroll
+            for (int p = 1; p < 6; ++p)
+                s = fma(Tb[i][p], T[l][p], s);
+            P[i][l] = s;
+        }
+    if (kG) {
+        double Y[6];
+#pragma unroll
+        for (int p = 0; p < 6; ++p)
+            Y[p] = ld_opt(a.gout[OUT_GINV + p], x);
+        adj_add_hAY<kIntMul>(h, Y, P);
+    }
+    double F[6];
+    adj_fold_PH<kIntMul>(P, H, F);
+#pragma unroll
+    for (int p = 0; p < 6; ++p)
+        st_stream(a.gin[IN_G + p] + x, neg_exact(F[p]));
+}
+
 }  // namespace tl

@@ -124,11 +124,20 @@ __global__ void __launch_bounds__(kFwdBwdThreads, 3) dtg_fwdbwd_f64_kernel(const
 // The same pass with the float-float arithmetic of TL_F64_FF: the inverse, the Eq. 6 bracket, the
 // folds of the upstream gradients and Eq. 5 in binary64, every contraction -- Eq. 6 and the footnote in
 // the forward, betabar, Gammabar, Tbar, the bracket's scatter and the folded -H A H in the adjoint --
-// in float-float pairs reusing the forward's h, T and Gamma.  A point with a value outside the pair
-// format's range is evaluated again, outputs and gradients, by the binary64 pass.
+// in float-float pairs reusing the forward's h, T and Gamma.  A point whose inputs fall outside the
+// pair format's range is evaluated again, outputs and gradients, by the binary64 pass (the float-float
+// forward takes binary64 for such a point too); one whose upstream gradients or S do keeps its outputs
+// and takes its gradients from the binary64 adjoint.
 template <bool kU, bool kG> __device__ __noinline__ void fwdbwd_point_f64_general(const FwdBwdArgs<double> &a, int64_t x)
 {
     fwdbwd_point_f64<kU, kG>(a, x);
+}
+
+// The gradients alone, by the binary64 adjoint's body (the same bits as tl_dtg_backward with TL_F64),
+// for a point whose float-float outputs are already stored.
+template <bool kU, bool kG> __device__ __noinline__ void fwdbwd_point_grad_f64(const FwdBwdArgs<double> &a, int64_t x)
+{
+    bwd_point_f64<kU, kG, false>(a, x);
 }
 
 template <bool kU, bool kG>
@@ -167,8 +176,8 @@ __device__ __forceinline__ void fwdbwd_point_ff(const FwdBwdArgs<double> &a, int
 #pragma unroll
     for (int p = 0; p < 6; ++p)
         Sf[p] = split_ff(S[p], big);
-    if (big) {
-        fwdbwd_point_f64_general<kU, kG>(a, x);
+    if (big) {   // the outputs stand; the gradients come from the binary64 adjoint
+        fwdbwd_point_grad_f64<kU, kG>(a, x);
         return;
     }
 

@@ -138,25 +138,32 @@ def test_fused_ff_ragged_and_conformal(n):
 
 
 def test_fused_ff_binary64_fallback():
-    """Points with an input (beta_0 = 2^70) or an upstream gradient (a Gamma^0_12 upstream gradient of
-    1e200) outside the pair range take the binary64 pass: their outputs and gradients are bit for bit
-    those of the binary64 fused pass, and the points whose inputs are in range keep the float-float
-    outputs.  The oracle gates the points 0-8 and the untouched ones; at the points 8-16 its own sum
-    adds and removes terms of ~1e199 (the two halves of the bracket's d_2 g_12 - d_2 g_21) and drops
-    the O(1) terms between them, so the exact gradient there is the one without cancellation."""
+    """Points whose inputs fall outside the pair range (beta_0 = 2^70) are evaluated in binary64, outputs
+    and gradients: bit for bit the binary64 fused pass (the float-float forward also takes binary64
+    there).  Points whose upstream gradients do (a Gamma^0_12 upstream gradient of 1e200) keep their
+    float-float outputs and take their gradients from the binary64 adjoint, bit for bit those of
+    tl_dtg_backward.  So the outputs equal the float-float forward's at every point.  The oracle gates
+    the untouched points and the points 0-8; at the points 8-16 its own sum adds and removes terms of
+    ~1e199 (the two halves of the bracket's d_2 g_12 - d_2 g_21) and drops the O(1) terms between
+    them, so the exact gradient there is the one without cancellation."""
+    import paper_1804_10120_gb300 as tl
     n = 2048
     x = gridgen.random_grid(n, 44)
     x[31, 0:8] = 2.0 ** 70
     gout = upstream(n, 45, ("ginv", "gamma", "dbcov", "dtg"))
     gout[6 + 4][8:16] = 1e200
     y, gin, y_sep = run_fused_ff(x, gout)
+    assert np.array_equal(y.view(np.uint64), y_sep.view(np.uint64))
     ref = oracle.backward(x, gout)
     for lo, hi in [(0, 8), (16, n)]:
         assert_components(gin[:, lo:hi], ref[:, lo:hi], TOL_F64, names=IN_NAMES, what="fused ff rows %d-%d" % (lo, hi))
-    assert np.array_equal(y[:, 16:].view(np.uint64), y_sep[:, 16:].view(np.uint64))
     y64, gin64, _ = run_fused(x, gout)
-    assert np.array_equal(y[:, 0:16].view(np.uint64), y64[:, 0:16].view(np.uint64))
-    assert np.array_equal(gin[:, 0:16].view(np.uint64), gin64[:, 0:16].view(np.uint64))
+    assert np.array_equal(y[:, 0:8].view(np.uint64), y64[:, 0:8].view(np.uint64))
+    assert np.array_equal(gin[:, 0:8].view(np.uint64), gin64[:, 0:8].view(np.uint64))
+    xd = torch.from_numpy(x).to(dev())
+    gd = [None if g is None else torch.from_numpy(g).to(dev()) for g in gout]
+    gb = tl.tl_dtg_backward(xd, gd).cpu().numpy()
+    assert np.array_equal(gin[:, 8:16].view(np.uint64), gb[:, 8:16].view(np.uint64))
 
 
 def test_fused_ff_full_size():
