@@ -260,3 +260,39 @@ def test_staging_rejects_what_is_not_provided():
         plan.set_staging(2)
     assert e.value.status == 3
     plan.close()
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f64_ff", "f32"])
+def test_empty_and_one_point_grids_inside_a_batch(dtype):
+    """Empty and one-point grids between ordinary ones, at every block size, blocks per SM and points
+    per thread: each grid bit for bit the single-grid kernel's (the empty ones untouched), and the
+    plan's status word clean."""
+    import paper_1804_10120_gb300 as tl
+    tdt = torch.float32 if dtype == "f32" else torch.float64
+    sides = [0, 1, 0, 0, 5, 1, 0, 9, 0, 1, 3, 0]
+    hosts, xs, ys = make_batch(sides, 31, dtype=tdt)
+    refs = [tl.tl_dtg_forward(x, dtype=dtype) for x in xs]
+    plan = tl.BatchPlan(xs, ys, dtype=dtype)
+    torch.cuda.synchronize()
+    ran = 0
+    for threads in (128, 256, 512):
+        for bps in (1, 2):
+            for ppt in (1, 2, 4):
+                try:
+                    plan.set_config(threads, bps, ppt)
+                except tl.TLError as e:          # beyond this kernel's occupancy
+                    assert e.status == 1
+                    continue
+                for y in ys:
+                    y.fill_(float("nan"))
+                plan.launch()
+                torch.cuda.synchronize()
+                ran += 1
+                for y, r in zip(ys, refs):
+                    assert torch.equal(y.view(torch.int64 if dtype != "f32" else torch.int32),
+                                       r.view(torch.int64 if dtype != "f32" else torch.int32)), (threads, bps, ppt)
+    assert ran > 0
+    plan.check()
+    assert_components(ys[7].double().cpu().numpy(), oracle.forward(hosts[7]),
+                      TOL_F64 if dtype != "f32" else 5e-6, what="9^3 grid")
+    plan.close()

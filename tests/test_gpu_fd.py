@@ -60,3 +60,25 @@ def test_fd_argument_checks():
         tl.tl_dtg_forward_fd(f, (3, 3, 3), (0.1, 0.0, 0.1))
     with pytest.raises(tl.TLError):
         tl.tl_dtg_forward_fd(f, (3, 3, 3), (0.1, 0.1, 0.1), dtype="f32")
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f64_ff"])
+@pytest.mark.parametrize("order", [2, 4])
+def test_fd_constant_fields_give_exact_zeros(order, dtype):
+    """Fields constant over the grid (a constant non-diagonal metric, K, alpha, beta): every difference
+    is exactly zero, so Gamma and nabla beta are exactly 0 and d_t g_ij = -2 alpha K_ij to the last bit
+    of the oracle's value; g^ij within the binary64 gate of the oracle."""
+    import paper_1804_10120_gb300 as tl
+    shape = (9, 7, 5)
+    n = 9 * 7 * 5
+    const = np.array([1.2, 0.1, -0.05, 0.9, 0.07, 1.1,            # g (SPD)
+                      0.3, -0.2, 0.1, 0.25, -0.15, 0.05,          # K
+                      0.8,                                        # alpha
+                      0.4, -0.3, 0.2])                            # beta
+    f = np.repeat(const[:, None], n, axis=1)
+    y = tl.tl_dtg_forward_fd(torch.from_numpy(f).to(torch.device("cuda", 0)), shape, (0.1, 0.2, 0.3), order,
+                             dtype=dtype).cpu().numpy()
+    assert np.all(y[6:33] == 0.0)                                 # Gamma and nabla beta
+    ref = oracle.forward(oracle.fd_inputs(f, shape, (0.1, 0.2, 0.3), order))
+    assert np.array_equal(y[33:39], ref[33:39])                   # -2 alpha K, one exact scaling and a product
+    assert_components(y, ref, TOL_F64, what="constant fields")

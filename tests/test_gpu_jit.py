@@ -195,3 +195,19 @@ def test_generated_chain_full_size():
     assert_components(yg, oracle.forward(np.ascontiguousarray(x[:, idx])), TOL_F64, what="generated chain, N=2^24")
     del y_gen, y_hand, xd
     k.close()
+
+
+@pytest.mark.parametrize("which", ["chain", "chain_sym"])
+def test_generated_chain_conformal_grid_exact_zeros(which):
+    """Conformally flat metric with beta = K = 0: the generated chain's nabla beta and d_t g vanish
+    exactly, as the hand kernel's do, and Gamma matches the oracle."""
+    import paper_1804_10120_gb300 as tl
+    from paper_1804_10120_gb300.programs import CHAIN, CHAIN_SYM
+    x = gridgen.conformal_grid(24)
+    k = tl.JitKernel(CHAIN if which == "chain" else CHAIN_SYM)
+    y = k.launch(torch.from_numpy(x).to(dev()))
+    torch.cuda.synchronize()
+    y = y.cpu().numpy()
+    assert np.all(y[24:39] == 0.0)
+    assert_components(y, oracle.forward(x), TOL_F64, what="generated %s, conformal" % which)
+    k.close()
