@@ -218,10 +218,18 @@ def launcher_check(args):
     import gridgen
     world, rank, _ = dist_setup()
     t0 = time.perf_counter()
-    x = gridgen.random_grid(4096, rank_seed(rank))
-    digest = hashlib.sha256(x.tobytes()).hexdigest()[:16]
+    if args.only == "batched":
+        # the sharded multi-domain batch: this rank's subgrids by the LPT rule, and their point count
+        from paper_1804_10120_gb300.shard import lpt_partition
+        sides = gridgen.subgrid_sides(args.grids, 2)
+        mine = lpt_partition([s ** 3 for s in sides], world)[rank]
+        digest = hashlib.sha256(json.dumps(mine).encode()).hexdigest()[:16]
+        views = [(rank, len(mine), sum(sides[d] ** 3 for d in mine), digest)]
+    else:
+        x = gridgen.random_grid(4096, rank_seed(rank))
+        digest = hashlib.sha256(x.tobytes()).hexdigest()[:16]
+        views = [(rank, rank_seed(rank), digest)]
     local_ms = (time.perf_counter() - t0) * 1e3
-    views = [(rank, rank_seed(rank), digest)]
     if world > 1:
         import torch
         import torch.distributed as dist
@@ -239,8 +247,12 @@ def launcher_check(args):
     else:
         t_max = local_ms
     if rank == 0:
+        if args.only == "batched":
+            ranks = [{"rank": r, "grids": g, "points": p, "indices_sha": d} for r, g, p, d in views]
+        else:
+            ranks = [{"rank": r, "seed": s, "grid_sha": d} for r, s, d in views]
         print(json.dumps({"launcher_check": True, "n_gpus": world, "gpus_arg": args.gpus, "t_max_ms": t_max,
-                          "ranks": [{"rank": r, "seed": s, "grid_sha": d} for r, s, d in views]}), flush=True)
+                          "ranks": ranks}), flush=True)
 
 
 def cpu_threads():
@@ -732,14 +744,21 @@ def extras(dev, stream, steps, x64, hbm, fp64_rates=None):
 def only_form(args):
     """One form alone, for profilers: forward (--variant), adjoint (loss W dtg + V Gamma), batched
     (--grids subgrids of the multi-domain recipe), fd (derivatives on a periodic cube of about --n
-    points, --order) or generated (the chain program through the runtime generator)."""
+    points, --order) or generated (the chain program through the runtime generator).  Under several
+    ranks the batched form splits its subgrids across them; the other forms run one replica each."""
     import torch
     import gridgen
     import paper_1804_10120_gb300 as tl
     from paper_1804_10120_gb300 import build as tlbuild
-    tlbuild.build()
-    dev = torch.device("cuda", 0)
+    world, rank, local = dist_setup()
+    if rank == 0 or world == 1:
+        tlbuild.build()
+    dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
+    if world > 1:
+        torch.distributed.init_process_group("nccl", device_id=dev)
+        torch.distributed.barrier()
+        tlbuild.build()
     stream = torch.cuda.current_stream(dev)
     n = args.n
     if args.only == "forward":
@@ -784,17 +803,32 @@ def only_form(args):
         fn = lambda: k.launch(x, y, stream=stream)
         units = n
     else:
+        # the multi-domain batch; under several ranks each GPU takes its share of the subgrids by the
+        # LPT rule (strong scaling: the same 600 subgrids in total, no exchange between the ranks)
+        from paper_1804_10120_gb300.shard import lpt_partition
         sides = gridgen.subgrid_sides(args.grids, 2)
+        mine = lpt_partition([s ** 3 for s in sides], world)[rank]
         xs, ys = [], []
-        for d, side in enumerate(sides):
+        for d in mine:
+            side = sides[d]
             xs.append(padded_rows(torch.from_numpy(gridgen.random_grid(side ** 3, 2, stream_base=gridgen.STREAMS_PER_FIELD * d)), dev))
             ys.append(padded_rows(torch.empty((39, side ** 3), dtype=torch.float64), dev))
         plan = tl.BatchPlan(xs, ys, dtype=args.variant if args.variant != "f32" else "f64")
         fn = lambda: plan.launch(stream)
         units = sum(side ** 3 for side in sides)
+    if world > 1:
+        torch.distributed.barrier()
     ms = cuda_time(fn, args.steps, stream, warmup=args.warmup)
-    print(json.dumps({"form": args.only, "variant": args.variant, "points": units, "ms": ms,
-                      "points_per_s": units / ms * 1e3}), flush=True)
+    if world > 1:
+        ms = _max_over_ranks(ms, dev)
+    if rank == 0:
+        line = {"form": args.only, "variant": args.variant, "points": units, "ms": ms,
+                "points_per_s": units / ms * 1e3}
+        if world > 1:
+            line.update({"n_gpus": world, "scaling": "strong" if args.only == "batched" else "weak"})
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
 
 
 EXPR_NAMES = {9: "A_i=B_i", 10: "A_ij=B_ij", 11: "A_ijk=B_ijk", 12: "A_i=B_i+C_i", 13: "A_i=B_i+C_i+D_i",

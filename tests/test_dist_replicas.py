@@ -92,3 +92,55 @@ def test_bench_refuses_world_size_that_contradicts_gpus():
     r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--gpus", "4", "--launcher-check"],
                        capture_output=True, text=True, timeout=120, env=env)
     assert r.returncode == 2 and "WORLD_SIZE=1" in r.stderr
+
+
+def test_lpt_partition_covers_and_balances():
+    """The longest-processing-time split of a multi-domain batch: every subgrid on exactly one part,
+    deterministic, and the largest share within the largest subgrid of the average share."""
+    import random
+    from paper_1804_10120_gb300.shard import lpt_partition
+    import gridgen
+    sizes = [s ** 3 for s in gridgen.subgrid_sides(600, 2)]
+    for parts in (1, 2, 3, 8):
+        split = lpt_partition(sizes, parts)
+        assert len(split) == parts
+        flat = sorted(i for p in split for i in p)
+        assert flat == list(range(len(sizes)))
+        loads = [sum(sizes[i] for i in p) for p in split]
+        assert max(loads) <= sum(sizes) / parts + max(sizes)
+        assert split == lpt_partition(sizes, parts)
+    assert lpt_partition([5, 5, 5], 2) == [[0, 2], [1]]          # ties: lower index first, lower part first
+    assert lpt_partition([3, 1], 4) == [[0], [1], [], []]
+    assert lpt_partition([], 3) == [[], [], []]
+    rng = random.Random(4)
+    for _ in range(50):
+        sz = [rng.randint(0, 1000) for _ in range(rng.randint(1, 40))]
+        m = rng.randint(1, 6)
+        loads = [sum(sz[i] for i in p) for p in lpt_partition(sz, m)]
+        assert sum(loads) == sum(sz) and max(loads) <= sum(sz) / m + max(sz)
+    with pytest.raises(ValueError):
+        lpt_partition([1], 0)
+    with pytest.raises(ValueError):
+        lpt_partition([-1], 2)
+
+
+def test_bench_batched_form_shards_the_subgrids_across_ranks():
+    """`bench.py --gpus 2 --only batched --launcher-check`: the two ranks (gloo on the CPU) hold disjoint
+    LPT shares of the 600 subgrids whose point counts add up to the whole batch."""
+    import json
+    import subprocess
+    import sys
+    import gridgen
+    from paper_1804_10120_gb300.shard import lpt_partition
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = {k: v for k, v in os.environ.items() if k not in ("WORLD_SIZE", "RANK", "LOCAL_RANK")}
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--gpus", "2", "--only", "batched",
+                        "--launcher-check"], capture_output=True, text=True, timeout=300, env=env)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = [json.loads(s) for s in r.stdout.splitlines() if s.startswith("{")][0]
+    ranks = sorted(line["ranks"], key=lambda v: v["rank"])
+    sizes = [s ** 3 for s in gridgen.subgrid_sides(600, 2)]
+    assert sum(v["grids"] for v in ranks) == 600 and sum(v["points"] for v in ranks) == sum(sizes)
+    split = lpt_partition(sizes, 2)
+    assert [v["points"] for v in ranks] == [sum(sizes[i] for i in p) for p in split]
+    assert ranks[0]["indices_sha"] != ranks[1]["indices_sha"]
