@@ -56,16 +56,26 @@ struct ChainF64Keep {
 // The chain on one point's 43 input values (in registers, in the input-table order); the 39 outputs go
 // to o.out[s][x] (o: any argument block with an `out` table) and the intermediates to k.  kLate: the
 // entries of v from K_ij on (K, alpha, beta, d_j beta_i: 19 values that only steps 3 and 4 use) are
-// not yet loaded; they are read from o.in[s][x] just before step 3, so their registers are free while
-// the inverse and Eq. 6 are formed (the caller has prefetched them into L1).
+// not yet loaded; `late` fills them just before step 3 (by default from o.in[s][x], which the caller
+// has prefetched into L1), so their registers are free while the inverse and Eq. 6 are formed.
 // kScaled: the d_k g_ij and d_j beta_i entries of v are differences that still need one common factor
 // sd (a finite-difference stencil on a grid with equal spacings); sd is then applied once to
 // 1/2 g^il and fused into nabla_j beta_i instead of to each of the 27 derivatives.  kIntMul: the 37
 // products that are not fused into an FMA go to the integer pipes (mul_int); the results are the same
 // bits either way.
-template <class OutTable, bool kScaled = false, bool kIntMul = true, bool kLate = false>
+// The late entries of v (K, alpha, beta, d_j beta_i) read from the input table o.in.
+struct LoadLate {
+    template <class OutTable> __device__ __forceinline__ void operator()(const OutTable &o, int64_t x, double (&vl)[N_IN]) const
+    {
+#pragma unroll
+        for (int s = IN_K; s < N_IN; ++s)
+            vl[s] = ld_stream(o.in[s] + x);
+    }
+};
+
+template <class OutTable, bool kScaled = false, bool kIntMul = true, bool kLate = false, class Late = LoadLate>
 __device__ __forceinline__ void chain_f64_keep(const double (&v0)[N_IN], const OutTable &o, int64_t x, double sd,
-                                               ChainF64Keep &k)
+                                               ChainF64Keep &k, const Late &late = Late())
 {
     double vl[N_IN];
 #pragma unroll
@@ -119,9 +129,7 @@ __device__ __forceinline__ void chain_f64_keep(const double (&v0)[N_IN], const O
 
     if constexpr (kLate) {
         asm volatile("" ::: "memory");   // the late inputs are loaded here, not hoisted above Eq. 6
-#pragma unroll
-        for (int s = IN_K; s < N_IN; ++s)
-            vl[s] = ld_stream(o.in[s] + x);
+        late(o, x, vl);
     }
     // step 3: nabla_j beta_i = d_j beta_i - Gamma^k_ij beta_k.  Gamma^k_ij beta_k is symmetric in ij, so
     // its 6 distinct sums are formed once (a product and 2 FMAs each) and subtracted from the 9
