@@ -152,7 +152,8 @@ __global__ void __launch_bounds__(kFwdThreads) dtg_fwd_f32_kernel(const FwdArgs<
 // counted in bytes on one mbarrier per stage, and the loads overlap the arithmetic of earlier tiles.
 // 512 points x 2 stages (176 KB: one block, 16 warps per SM) measured best, 0.94 ms at N = 2^24
 // against 1.00 ms for the plain kernel; 256 x 4 and 384 x 3 (8 and 12 warps) leave the binary64
-// inverse latency-bound, and 640 x 2 or 768 x 2 (K and alpha then read directly) were slower.
+// inverse latency-bound, and 640 x 2 or 768 x 2 (K and alpha then read directly) were slower, as were
+// 256 x 2 at two blocks per SM (1.05 ms) and 128 x 3 at three (1.18 ms).
 // Each block walks tiles blockIdx.x, + gridDim.x, ...
 // One __syncthreads per tile (after the wait) certifies that every thread has finished the previous
 // tile, whose stage is then refilled.  Requires 16-byte aligned input streams; the last n % TILE
