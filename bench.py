@@ -381,11 +381,24 @@ def device_facts(dev):
 
 
 def nominal_hbm_gbs(dev):
-    """Nominal HBM bandwidth from the device properties: memory clock x 2 (double data rate) x bus width;
-    None when this PyTorch does not expose them."""
+    """Nominal HBM bandwidth from the device properties: memory clock x 2 (double data rate) x bus width
+    (from PyTorch's device properties, else the library's device query); None when neither has them."""
     import torch
     p = torch.cuda.get_device_properties(dev)
     khz, bits = getattr(p, "memory_clock_rate", None), getattr(p, "memory_bus_width", None)
+    if not khz or not bits:
+        try:
+            import ctypes
+            import paper_1804_10120_gb300 as tl
+            L = tl.lib()
+            L.tl_testing_memory_info.argtypes = [ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                                                 ctypes.POINTER(ctypes.c_int32)]
+            L.tl_testing_memory_info.restype = ctypes.c_int
+            c, b = ctypes.c_int32(), ctypes.c_int32()
+            if L.tl_testing_memory_info(dev.index or 0, ctypes.byref(c), ctypes.byref(b)) == 0:
+                khz, bits = c.value, b.value
+        except Exception:
+            khz = bits = None
     if not khz or not bits:
         return None
     return (khz * 1e3 * 2 * bits / 8 / 1e9,

@@ -70,6 +70,12 @@ TL_API tl_status tl_testing_pipe_rate(int op, int64_t iters, int32_t blocks, int
  * memory at its first launch on a device.  Host only.
  */
 TL_API tl_status tl_testing_jit_min_blocks(const tl_jit_kernel *k, int32_t *blocks);
+/*
+ * tl_testing_memory_info: the device's peak memory clock (kHz) and global memory bus width (bits), from
+ * which the nominal HBM bandwidth is clock x 2 x width / 8.  TL_ERR_INVALID_ARG for NULL outputs
+ * (checked before any CUDA call), TL_ERR_CUDA when the device cannot be queried.
+ */
+TL_API tl_status tl_testing_memory_info(int32_t device, int32_t *clock_khz, int32_t *bus_bits);
 
 #ifdef __cplusplus
 }

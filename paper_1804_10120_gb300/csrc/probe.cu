@@ -81,3 +81,18 @@ extern "C" TL_API tl_status tl_testing_pipe_rate(int op, int64_t iters, int32_t 
     }
     return cudaGetLastError() == cudaSuccess ? TL_OK : TL_ERR_CUDA;
 }
+
+extern "C" TL_API tl_status tl_testing_memory_info(int32_t device, int32_t *clock_khz, int32_t *bus_bits)
+{
+    if (!clock_khz || !bus_bits)
+        return TL_ERR_INVALID_ARG;
+    int c = 0, b = 0;
+    if (cudaDeviceGetAttribute(&c, cudaDevAttrMemoryClockRate, device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&b, cudaDevAttrGlobalMemoryBusWidth, device) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return TL_ERR_CUDA;
+    }
+    *clock_khz = c;
+    *bus_bits = b;
+    return TL_OK;
+}

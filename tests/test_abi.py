@@ -182,4 +182,14 @@ def test_bench_floor_and_nominal_bandwidth(monkeypatch):
     gbs, src = bench.nominal_hbm_gbs(None)
     assert abs(gbs - 3996e6 * 2 * 1024 / 1e9) < 1e-6 and "8192-bit" in src
     monkeypatch.setattr(torch.cuda, "get_device_properties", lambda dev: types.SimpleNamespace())
-    assert bench.nominal_hbm_gbs(None) is None
+    if not torch.cuda.is_available():
+        assert bench.nominal_hbm_gbs(torch.device("cuda", 0)) is None   # no device to query either
+
+
+def test_memory_info_argument_checks(L):
+    """The device memory query rejects NULL outputs before any CUDA call."""
+    f = L.tl_testing_memory_info
+    f.argtypes = [ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    v = ctypes.c_int32()
+    assert f(0, None, ctypes.byref(v)) == 1 and f(0, ctypes.byref(v), None) == 1

@@ -166,3 +166,23 @@ def test_pipe_rate_probe_runs_and_writes_nothing():
     per_s = blocks * threads * 8 * iters / (e0.elapsed_time(e1) * 1e-3)
     per_clk_sm = per_s / (sms * 2.07e9)                # at the highest SM clock of the part
     assert 0.5 < per_clk_sm < 2.2, per_clk_sm
+
+
+def test_memory_info_gives_the_nominal_hbm_bandwidth():
+    """The device memory query: clock x 2 x bus width / 8 is the part's nominal HBM bandwidth, above
+    the measured copy bandwidth (which reads a little below nominal)."""
+    import json
+    import os
+    import bench
+    import paper_1804_10120_gb300 as tl
+    L = tl.lib()
+    L.tl_testing_memory_info.argtypes = [ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
+    L.tl_testing_memory_info.restype = ctypes.c_int
+    c, b = ctypes.c_int32(), ctypes.c_int32()
+    assert L.tl_testing_memory_info(0, ctypes.byref(c), ctypes.byref(b)) == 0
+    gbs = c.value * 1e3 * 2 * b.value / 8 / 1e9
+    nominal = bench.nominal_hbm_gbs(torch.device("cuda", 0))
+    assert nominal is not None and abs(nominal[0] - gbs) < 1e-6 * gbs
+    peaks = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "MEASURED_PEAKS.json")
+    measured = json.load(open(peaks))["hbm_gbs"] if os.path.exists(peaks) else 6000.0
+    assert measured < gbs < 2 * measured, (gbs, measured)
